@@ -1,0 +1,320 @@
+"""Benchmark of the epipolar-adjustment hot path on GB300.
+
+One step = one IRLS round of the method: reweighting with filtering at the current poses
+(fm_irls_weights) followed by `--iters` optimiser iterations (loss + analytic gradient over
+every point pair, per-camera gradient, Adam + exponential map), all on the GPU.
+
+Default workload: the 4,000-camera trajectory scene (~1.5e8 point pairs, ~5e4 image pairs,
+Pareto match counts, 25% outliers), FP16 centroid-offset storage, FP32 arithmetic. The
+inputs (>1 GB) are larger than L2, so no flush is needed between timed iterations.
+
+Prints one JSON line. `value` counts point pairs evaluated by loss+gradient passes per second
+(G point-pairs/s); the reweighting pass of each round is inside the timed region but not
+counted. `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G point-pairs/s epipolar loss+grad (% HBM peak); time to rot err<0.1° learned vs IRLS"
+UNIT = "G point-pairs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="traj4000")
+    ap.add_argument("--storage", default="fp16", choices=["fp16", "fp32"])
+    ap.add_argument("--iters", type=int, default=25, help="optimiser iterations per IRLS round")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source (the summary records the source hash); else None."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2605_18052_gb300", "csrc", "fm_kernels.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_tag and parts[1] == h:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def schedule_for(sc, iters):
+    import numpy as np
+    from paper_2605_18052_gb300 import Schedule
+    R, t = sc.R_gt.double(), sc.t_gt.double()
+    C = -(R.transpose(1, 2) @ t[:, :, None])[:, :, 0]
+    base = float((C[sc.cam_i.long()] - C[sc.cam_j.long()]).norm(dim=1).median())
+    rounds = max(1, sc.iters // iters)
+    return Schedule(rounds=rounds, iters_per_round=iters, tau0=0.05, tau_min=4 * sc.sigma_px / sc.f,
+                    decay=0.9, lr_rot=1e-2, lr_c=1e-2 * base)
+
+
+def cpu_oracle_rate(sc, seconds: float):
+    """FP64 oracle loss+gradient on a bounded sample of whole image pairs (1 thread)."""
+    import numpy as np
+    import oracle as O
+    cnt = np.bincount(sc.pair_id.cpu().numpy(), minlength=sc.n_pairs)
+    target = 4_000_000
+    nb = int(np.searchsorted(np.cumsum(cnt), target)) + 1
+    nb = min(nb, sc.n_pairs)
+    npp = int(cnt[:nb].sum())
+    pid = sc.pair_id[:npp].cpu().numpy()
+    prob = O.Problem(sc.n_cams, sc.cam_i.cpu().numpy(), sc.cam_j.cpu().numpy(), pid,
+                     sc.x1[:npp].cpu().numpy(), sc.x2[:npp].cpu().numpy())
+    R0 = sc.R_init.cpu().numpy()
+    c0 = O.centres_from_poses(R0, sc.t_init.cpu().numpy())
+    w = np.ones(npp)
+    evals = 0
+    t0 = time.perf_counter()
+    while True:
+        O.loss_grad(prob, R0, c0, w)
+        evals += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return evals * npp / el / 1e9, f"first {nb} image pairs ({npp} point pairs), {evals} loss+grad evaluations"
+
+
+def run_reference(args, rank):
+    import torch
+    import scenegen
+    if rank != 0:
+        return
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    sc = scenegen.make_scene(args.config, seed=args.seed, device=dev).to("cpu")
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    sample = ""
+    for k in range(args.warmup + args.steps):
+        v, sample = cpu_oracle_rate(sc, per_step if k >= args.warmup else 0.5)
+        if k >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    npp_total = sc.n_pp
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": args.iters * npp_total / (value * 1e9) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded scene generator)",
+           "config": {"workload": f"{args.config} (FP64 CPU oracle, 1 thread)", "n_pp": npp_total,
+                      "n_pairs": sc.n_pairs, "n_cams": sc.n_cams, "iters_per_step": args.iters},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import scenegen
+    import paper_2605_18052_gb300 as fm
+    from paper_2605_18052_gb300 import build as fm_build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        fm_build.build()
+    if world > 1:
+        dist.barrier()
+    fm.load_library()
+
+    # each rank: its own seeded scene (weak scaling: replicas, no data-path collective)
+    sc = scenegen.make_scene(args.config, seed=args.seed + rank, device="cuda")
+    sch = schedule_for(sc, args.iters)
+    opt = fm.default_options(storage=args.storage, lr_rot=sch.lr_rot, lr_c=sch.lr_c)
+    stream = torch.cuda.current_stream()
+    gp = fm.Problem(sc.R_init.cpu(), sc.t_init.cpu(), sc.cam_i.cpu(), sc.cam_j.cpu(), sc.pair_id,
+                    sc.x1, sc.x2, options=opt)
+    info = gp.info()
+    n_pp = info["n_pp"]
+
+    def one_step(r):
+        gp.irls_weights(sch.tau(r % sch.rounds))
+        gp.step(args.iters)
+
+    for r in range(args.warmup):
+        one_step(r)
+    gp.synchronize()
+    gp.enable_kernel_timing(True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(args.steps):
+            one_step(args.warmup + k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    kern_ms, kern_n = gp.kernel_time()
+    gp.enable_kernel_timing(False)
+    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    pp_local = torch.tensor([float(n_pp) * args.iters * args.steps], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.all_reduce(pp_local, op=dist.ReduceOp.SUM)
+    ms_max = float(t_local.item())
+    value = float(pp_local.item()) / (ms_max * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (loss+gradient stream)
+    bytes_per_launch = info["stream_bytes"]
+    avg_launch_s = kern_ms * 1e-3 / max(1, kern_n)
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    peak, peak_kind = peaks()
+    tag = f"stream_loss_{args.storage}_{args.config}"
+    traffic = profiled_traffic(tag)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": f"k_stream_loss<{args.storage.upper()}, IRLS>",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs burst copy)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6}
+    launches = args.steps * (2 + 5 * args.iters)
+    clocks = clk.summary()
+
+    # end to end through the public API with pinned host buffers: create + full schedule + poses
+    e2e = None
+    if not args.no_e2e:
+        h = {k: getattr(sc, k).cpu().pin_memory() for k in ("pair_id", "x1", "x2")}
+        Rh, th = sc.R_init.cpu(), sc.t_init.cpu()
+        cih, cjh = sc.cam_i.cpu(), sc.cam_j.cpu()
+        del gp
+        torch.cuda.synchronize()
+        times = []
+        for k in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with fm.Problem(Rh, th, cih, cjh, h["pair_id"], h["x1"], h["x2"], options=opt) as jp:
+                fm.refine(jp, sch)
+                R_out, t_out = jp.get_poses()
+            times.append(time.perf_counter() - t0)
+        t_job = statistics.median(times[1:])
+        e2e_pp = float(n_pp) * sch.rounds * sch.iters_per_round
+        e2e = {"value": e2e_pp / t_job / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(n_pp * (4 + 8 + 8) + sc.n_cams * 12 * 8 + sc.n_pairs * 8),
+               "d2h_bytes_per_step": int(sc.n_cams * 12 * 8),
+               "job": f"fm_create_problem from pinned host buffers + {sch.rounds} rounds x {sch.iters_per_round} iterations + fm_get_poses",
+               "seconds_per_job": t_job}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, sample = cpu_oracle_rate(sc, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (seeded scene generator, trajectory scene shaped like the paper's large scenes)",
+               "config": {"workload": f"{args.config}: {sc.n_cams} cameras, {sc.n_pairs} image pairs, {n_pp} point pairs",
+                          "storage": args.storage, "iters_per_step": args.iters,
+                          "step": "1 IRLS reweighting pass + iters x (loss+grad, Adam)",
+                          "l2": "inputs larger than L2 (no flush needed)",
+                          "parallelism": f"replicas x{world}"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clocks, "hbm_frac_of_step": value * 1e9 * bytes_per_launch / n_pp / 1e9 / peak}
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * fastmap.h - C ABI of the GB300 epipolar-adjustment library (libfastmap.so).
+ *
+ * The library refines global camera poses by FastMap's re-weighting epipolar adjustment
+ * (Sec. "Epipolar Adjustment"): it minimises, over world-to-camera rotations and
+ * translations, the mean absolute epipolar error
+ *     L_e = (1/Z) sum_n sum_m | x2_nm^T E_n x1_nm |                (Eq. epipolar-objective)
+ * through iteratively re-weighted least squares
+ *     L^_e = (1/Z) sum_n sum_m w_nm (x2_nm^T E_n x1_nm)^2,  w_nm = 1/|eps^_nm|
+ * (the IRLS objective of the same section) with periodic filtering of point pairs whose
+ * error exceeds a shrinking threshold, using a first-order optimiser (Adam; Sec.
+ * "First-order Optimization"). Every per-point-pair pass runs in the library's CUDA kernels.
+ *
+ * Conventions shared by all entry points
+ *   - Camera k is world-to-camera: x_cam = R_k X + t_k; R is row-major 3x3, FP64. The
+ *     library optimises R_k (by left increments, R_k <- Exp(phi_k) R_k) and the camera
+ *     centre c_k = -R_k^T t_k. Poses cross the ABI as (R, t).
+ *   - Image pair n = (cam_i[n], cam_j[n]), cam_i != cam_j. Point pair p belongs to pair
+ *     pair_id[p]; x1[2p..2p+1] is its keypoint in image cam_i, x2[2p..2p+1] in image cam_j,
+ *     both in normalized image coordinates ((u - cx)/f, (v - cy)/f) (Sec. "Camera
+ *     Assumptions": principal point at the centre, intrinsics known).
+ *   - E_n = [t_n/|t_n|]_x R_n with R_n = R_j R_i^T, t_n = t_j - R_n t_i (the essential
+ *     matrix computed from the global poses; its translation is taken with unit length so
+ *     the objective is invariant to the global scale).
+ *   - Z = n_pp, the total number of point pairs (filtered pairs keep counting).
+ *   - Gradients are with respect to (phi_k, c_k) at phi = 0, FP64, n_cams x 6, ordered
+ *     [phi_x, phi_y, phi_z, c_x, c_y, c_z].
+ *   - "Input order" means the order of the point pairs passed to fm_create_problem.
+ *
+ * Ownership and streams
+ *   - fm_create_problem copies every input; the caller keeps its buffers. The problem owns
+ *     all device memory it allocates and frees it in fm_destroy_problem.
+ *   - Each problem runs its kernels on a private non-blocking stream, ordered after the
+ *     work already queued on the caller's stream at call time (the `stream` argument of
+ *     fm_create_problem, a cudaStream_t; NULL means the legacy default stream). Calls that
+ *     return host data block until that data is ready; fm_step only enqueues.
+ *   - A problem is not thread-safe; one host thread at a time may use it.
+ *
+ * Errors
+ *   - No C++ exception crosses the ABI. Every entry point returns fm_status; FM_OK is 0.
+ *   - Invalid arguments (NULL pointers, sizes out of range, pair indices out of range,
+ *     cam_i == cam_j, an image pair without point pairs, non-finite or |coordinate| > 8
+ *     keypoints) return FM_EINVAL and leave outputs untouched.
+ *   - Device-detected problems (a relative translation of zero length, non-finite
+ *     residuals) are recorded on the device and returned as FM_EDEGENERATE by the next call
+ *     that synchronises (fm_synchronize, fm_get_poses, fm_loss_grad, ...).
+ *   - fm_last_error() returns a thread-local message describing the last failure.
+ */
+#ifndef FASTMAP_H_
+#define FASTMAP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FM_API __attribute__((visibility("default")))
+#else
+#define FM_API
+#endif
+
+typedef struct fm_problem fm_problem;
+
+typedef enum {
+    FM_OK = 0,
+    FM_EINVAL = -1,      /* invalid argument or input data */
+    FM_ENOMEM = -2,      /* device or host allocation failed */
+    FM_ECUDA = -3,       /* a CUDA runtime call failed */
+    FM_EDEGENERATE = -4, /* zero-length relative translation or non-finite value on device */
+    FM_ESTATE = -5       /* call not valid in the problem's current state */
+} fm_status;
+
+/* Keypoint storage in device memory. */
+enum {
+    FM_STORE_FP32 = 0,   /* (x1, y1, x2, y2) as 4 x FP32 = 16 B per point pair + FP32 weight */
+    FM_STORE_FP16 = 1    /* FP16 offsets from per-image centroids, 8 B + FP16 weight (2 B) */
+};
+
+/* Objective minimised by fm_step and returned by fm_loss_grad. */
+enum {
+    FM_LOSS_IRLS = 0,    /* (1/Z) sum w eps^2 with the current weights (all 1 until reweighted) */
+    FM_LOSS_L1 = 1       /* (1/Z) sum |eps| */
+};
+
+typedef struct {
+    int32_t storage;     /* FM_STORE_FP32 or FM_STORE_FP16 */
+    int32_t loss;        /* FM_LOSS_IRLS or FM_LOSS_L1 */
+    double delta;        /* IRLS weight floor: w = 1/max(|eps^|, delta); > 0 */
+    double lr_rot;       /* Adam step size for phi (radians) */
+    double lr_c;         /* Adam step size for camera centres (scene units) */
+    double beta1, beta2; /* Adam moment decay rates, in [0, 1) */
+    double adam_eps;     /* Adam denominator epsilon, >= 0 */
+    int32_t use_graph;   /* 1: replay one captured CUDA graph per iteration in fm_step */
+    int32_t reserved;    /* must be 0 */
+} fm_options;
+
+typedef struct {
+    int32_t n_cams, n_pairs;
+    int64_t n_pp;
+    int32_t storage, loss;
+    int64_t n_warp_ranges;      /* work units of the streaming kernels */
+    int64_t stream_bytes;       /* algorithmic bytes read by one loss+gradient pass */
+    int64_t device_bytes;       /* device memory held by the problem */
+    int32_t input_was_sorted;   /* 1 if point pairs arrived grouped by pair_id */
+    int32_t reserved;
+} fm_info;
+
+/* Defaults: FP32 storage, IRLS loss, delta 1e-6, lr_rot 1e-2, lr_c 1e-2, betas 0.9/0.999,
+ * adam_eps 1e-12, use_graph 1. */
+FM_API void fm_default_options(fm_options *opt);
+
+/*
+ * Build a problem (Sec. "Epipolar Adjustment": image pairs P = {(i_n, j_n)} and point-pair
+ * sets Q_n). R (n_cams x 9) and t (n_cams x 3) are the initial poses, host FP64.
+ * cam_i, cam_j (n_pairs) are host int32. pair_id (n_pp, int32), x1, x2 (n_pp x 2, FP32)
+ * are host pointers, or device pointers when pp_on_device is 1. Point pairs may come in
+ * any order; they are sorted by pair on the device (stable). Requires n_cams >= 2,
+ * n_pairs >= 1, 1 <= n_pp < 2^31 - 2^16. Blocks until the device layout is built.
+ */
+FM_API fm_status fm_create_problem(int32_t n_cams, const double *R, const double *t,
+                                   int32_t n_pairs, const int32_t *cam_i, const int32_t *cam_j,
+                                   int64_t n_pp, const int32_t *pair_id, const float *x1,
+                                   const float *x2, int32_t pp_on_device, const fm_options *opt,
+                                   void *stream, fm_problem **out);
+
+/* Free all device and host memory of the problem (after finishing its queued work). */
+FM_API void fm_destroy_problem(fm_problem *p);
+
+FM_API fm_status fm_problem_info(const fm_problem *p, fm_info *info);
+
+/* Current poses (host FP64, R n_cams x 9, t n_cams x 3). Synchronises. */
+FM_API fm_status fm_get_poses(fm_problem *p, double *R, double *t);
+/* Replace the poses (host FP64); keeps the optimiser state. */
+FM_API fm_status fm_set_poses(fm_problem *p, const double *R, const double *t);
+
+/*
+ * The optimiser's own parameters: rotations R (n_cams x 9) and camera centres c (n_cams x 3),
+ * host FP64, copied without conversion. Together with fm_get_state/fm_set_state and the
+ * weights they make an exact checkpoint (fm_get_poses/fm_set_poses convert t = -R c and
+ * round in the last bit). fm_get_params synchronises.
+ */
+FM_API fm_status fm_get_params(fm_problem *p, double *R, double *c);
+FM_API fm_status fm_set_params(fm_problem *p, const double *R, const double *c);
+
+/*
+ * Replace the per-point-pair weights w of the IRLS objective (n_pp FP32, input order; host,
+ * or device when on_device is 1). FP16 storage keeps fp16_rn(w * s)/s with the power of
+ * two s = 2^floor(log2(32768 * delta)); weights must be finite and in [0, 1/delta].
+ */
+FM_API fm_status fm_set_weights(fm_problem *p, const float *w, int32_t on_device);
+/* Current weights as stored (n_pp FP32, input order, host). Synchronises. */
+FM_API fm_status fm_get_weights(fm_problem *p, float *w);
+
+/*
+ * IRLS reweighting with outlier filtering at the current poses (Sec. "Epipolar Adjustment",
+ * IRLS and filtering paragraphs): eps^ = x2^T E_n x1 for every point pair, then
+ * w = 1/max(|eps^|, delta) if |eps^| <= tau, else w = 0. tau may be +inf (no filtering).
+ * Writes the number of kept point pairs to *n_active (may be NULL). Synchronises.
+ */
+FM_API fm_status fm_irls_weights(fm_problem *p, double tau, int64_t *n_active);
+
+/*
+ * Objective and gradient at the current poses with the current weights (the objective
+ * selected by opt.loss). loss: host FP64 scalar; grad: host FP64 n_cams x 6 (may be NULL).
+ * Synchronises.
+ */
+FM_API fm_status fm_loss_grad(fm_problem *p, double *loss, double *grad);
+/* Same, asynchronous, into device memory the caller owns (either pointer may be NULL). */
+FM_API fm_status fm_loss_grad_device(fm_problem *p, double *d_loss, double *d_grad);
+
+/* Residuals eps = x2^T E_n x1 at the current poses, FP32, input order, host. Synchronises. */
+FM_API fm_status fm_residuals(fm_problem *p, float *eps);
+
+/*
+ * n_iters optimiser iterations, each: objective gradient at the current poses, one Adam
+ * step on (phi_k, c_k), R_k <- Exp(phi_k) R_k with FP64 re-orthonormalisation. Only
+ * enqueues work; errors found on the device surface at the next synchronising call.
+ */
+FM_API fm_status fm_step(fm_problem *p, int32_t n_iters);
+
+/* Objective value of the most recent iteration of fm_step (or fm_loss_grad). Synchronises. */
+FM_API fm_status fm_last_loss(fm_problem *p, double *loss);
+
+/* Change the Adam step sizes used by later iterations (a learning-rate schedule). */
+FM_API fm_status fm_set_learning_rate(fm_problem *p, double lr_rot, double lr_c);
+
+/* Zero the Adam moments and the step counter. */
+FM_API fm_status fm_reset_optimizer(fm_problem *p);
+
+/*
+ * Optimiser state for checkpoint/resume: m and v (n_cams x 6 FP64 each, host) and the
+ * 1-based number of Adam steps taken. Resuming from a saved (poses, weights, state) gives
+ * bit-identical trajectories because every reduction runs in a fixed order.
+ */
+FM_API fm_status fm_get_state(fm_problem *p, double *m, double *v, int64_t *step);
+FM_API fm_status fm_set_state(fm_problem *p, const double *m, const double *v, int64_t step);
+
+/* Wait for all queued work of the problem; returns FM_EDEGENERATE if the device flagged one. */
+FM_API fm_status fm_synchronize(fm_problem *p);
+
+/*
+ * Kernel timing: when enabled, fm_step records CUDA events around every launch of the
+ * loss+gradient streaming kernel (and replays no graph). fm_kernel_time returns the summed
+ * event time in milliseconds and the number of timed launches since enabling, and resets
+ * both. Synchronises.
+ */
+FM_API fm_status fm_enable_kernel_timing(fm_problem *p, int32_t enable);
+FM_API fm_status fm_kernel_time(fm_problem *p, double *ms, int64_t *launches);
+
+FM_API const char *fm_status_string(fm_status s);
+FM_API const char *fm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTMAP_H_ */

@@ -284,10 +284,18 @@ def fp16_centroid_storage(prob: Problem, x1_f32, x2_f32):
     cj = prob.cam_j[prob.pair_id]
     S = np.zeros((prob.n_cams, 2), dtype=np.int64)
     cnt = np.zeros(prob.n_cams, dtype=np.int64)
-    for cam, x in ((ci, x1), (cj, x2)):
-        fx = np.trunc(x.astype(np.float64) * 2.0 ** FIXED_POINT_SHIFT).astype(np.int64)
-        np.add.at(S, cam, fx)
-        np.add.at(cnt, cam, 1)
+    # exact integer sums: per image pair first (segments of the pair-sorted list), then per image
+    order = None if np.all(prob.pair_id[1:] >= prob.pair_id[:-1]) else np.argsort(prob.pair_id, kind="stable")
+    pid = prob.pair_id if order is None else prob.pair_id[order]
+    starts = np.flatnonzero(np.r_[True, pid[1:] != pid[:-1]])
+    seg_pair = pid[starts]
+    seg_cnt = np.diff(np.r_[starts, len(pid)])
+    for cams, x in ((prob.cam_i, x1), (prob.cam_j, x2)):
+        xs = x if order is None else x[order]
+        fx = np.trunc(xs.astype(np.float64) * 2.0 ** FIXED_POINT_SHIFT).astype(np.int64)
+        seg_sum = np.add.reduceat(fx, starts, axis=0)
+        np.add.at(S, cams[seg_pair], seg_sum)
+        np.add.at(cnt, cams[seg_pair], seg_cnt)
     cen = np.zeros((prob.n_cams, 2), dtype=np.float32)
     has = cnt > 0
     cen[has] = ((S[has].astype(np.float64) / cnt[has, None].astype(np.float64))

@@ -1,0 +1,11 @@
+"""GB300 epipolar pose adjustment (the hot path of FastMap's structure-from-motion stage).
+
+The CUDA library libfastmap.so (C ABI in include/fastmap.h) holds the problem on the GPU and
+runs every per-point-pair pass; this package is its Python binding plus host-side drivers.
+"""
+from .binding import (FM_LOSS_IRLS, FM_LOSS_L1, FM_STORE_FP16, FM_STORE_FP32, FastMapError,
+                      Options, Problem, default_options, load_library)
+from .refine import Schedule, refine
+
+__all__ = ["Problem", "Options", "default_options", "load_library", "FastMapError", "Schedule",
+           "refine", "FM_STORE_FP32", "FM_STORE_FP16", "FM_LOSS_IRLS", "FM_LOSS_L1"]

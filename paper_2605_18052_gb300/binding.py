@@ -1,0 +1,296 @@
+"""ctypes binding of libfastmap (include/fastmap.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels. If the library is missing this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfastmap.so")
+
+FM_STORE_FP32, FM_STORE_FP16 = 0, 1
+FM_LOSS_IRLS, FM_LOSS_L1 = 0, 1
+
+EXPORTED = [
+    "fm_default_options", "fm_create_problem", "fm_destroy_problem", "fm_problem_info",
+    "fm_get_poses", "fm_set_poses", "fm_get_params", "fm_set_params", "fm_set_weights", "fm_get_weights", "fm_irls_weights",
+    "fm_loss_grad", "fm_loss_grad_device", "fm_residuals", "fm_step", "fm_last_loss",
+    "fm_set_learning_rate", "fm_reset_optimizer", "fm_get_state", "fm_set_state",
+    "fm_synchronize", "fm_enable_kernel_timing", "fm_kernel_time", "fm_status_string",
+    "fm_last_error",
+]
+
+
+class FastMapError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int32), ("loss", ctypes.c_int32), ("delta", ctypes.c_double),
+                ("lr_rot", ctypes.c_double), ("lr_c", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_cams", ctypes.c_int32), ("n_pairs", ctypes.c_int32), ("n_pp", ctypes.c_int64),
+                ("storage", ctypes.c_int32), ("loss", ctypes.c_int32),
+                ("n_warp_ranges", ctypes.c_int64), ("stream_bytes", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("input_was_sorted", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfastmap.so (built by paper_2605_18052_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FastMapError(-3, f"{path} is missing: build it with paper_2605_18052_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "fm_default_options": (None, [P]),
+        "fm_create_problem": (I32, [I32, P, P, I32, P, P, I64, P, P, P, I32, P, P, P]),
+        "fm_destroy_problem": (None, [P]),
+        "fm_problem_info": (I32, [P, P]),
+        "fm_get_poses": (I32, [P, P, P]),
+        "fm_set_poses": (I32, [P, P, P]),
+        "fm_get_params": (I32, [P, P, P]),
+        "fm_set_params": (I32, [P, P, P]),
+        "fm_set_weights": (I32, [P, P, I32]),
+        "fm_get_weights": (I32, [P, P]),
+        "fm_irls_weights": (I32, [P, D, P]),
+        "fm_loss_grad": (I32, [P, P, P]),
+        "fm_loss_grad_device": (I32, [P, P, P]),
+        "fm_residuals": (I32, [P, P]),
+        "fm_step": (I32, [P, I32]),
+        "fm_last_loss": (I32, [P, P]),
+        "fm_set_learning_rate": (I32, [P, D, D]),
+        "fm_reset_optimizer": (I32, [P]),
+        "fm_get_state": (I32, [P, P, P, P]),
+        "fm_set_state": (I32, [P, P, P, I64]),
+        "fm_synchronize": (I32, [P]),
+        "fm_enable_kernel_timing": (I32, [P, I32]),
+        "fm_kernel_time": (I32, [P, P, P]),
+        "fm_status_string": (ctypes.c_char_p, [I32]),
+        "fm_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        lib = load_library()
+        raise FastMapError(status, lib.fm_last_error().decode() or lib.fm_status_string(status).decode())
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load_library().fm_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "storage" and isinstance(v, str):
+            v = {"fp32": FM_STORE_FP32, "fp16": FM_STORE_FP16}[v]
+        if k == "loss" and isinstance(v, str):
+            v = {"irls": FM_LOSS_IRLS, "l1": FM_LOSS_L1}[v]
+        setattr(o, k, v)
+    return o
+
+
+def _host(a, dtype) -> np.ndarray:
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _is_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+class Problem:
+    """One epipolar-adjustment problem held on the GPU (see include/fastmap.h)."""
+
+    def __init__(self, R, t, cam_i, cam_j, pair_id, x1, x2, options: Options | None = None,
+                 stream=None):
+        lib = load_library()
+        R = _host(R, np.float64).reshape(-1, 9)
+        t = _host(t, np.float64).reshape(-1, 3)
+        ci = _host(cam_i, np.int32)
+        cj = _host(cam_j, np.int32)
+        self.n_cams = R.shape[0]
+        self.n_pairs = ci.shape[0]
+        on_dev = _is_cuda(pair_id)
+        if on_dev:
+            import torch
+            pid = pair_id.to(torch.int32).contiguous()
+            a = x1.to(torch.float32).contiguous()
+            b = x2.to(torch.float32).contiguous()
+            self._keep = (pid, a, b)
+            ptrs = [ctypes.c_void_p(pid.data_ptr()), ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr())]
+            n_pp = pid.numel()
+        else:
+            pid = _host(pair_id, np.int32)
+            a = _host(x1, np.float32)
+            b = _host(x2, np.float32)
+            ptrs = [_ptr(pid), _ptr(a), _ptr(b)]
+            n_pp = pid.shape[0]
+        self.n_pp = int(n_pp)
+        self.options = options if options is not None else default_options()
+        self.stream = stream if stream is not None else _current_stream()
+        h = ctypes.c_void_p()
+        _check(lib.fm_create_problem(self.n_cams, _ptr(R), _ptr(t), self.n_pairs, _ptr(ci), _ptr(cj),
+                                     self.n_pp, *ptrs, 1 if on_dev else 0, ctypes.byref(self.options),
+                                     self.stream, ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+
+    # -- lifecycle -------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().fm_destroy_problem(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load_library().fm_problem_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in Info._fields_ if f != "reserved"}
+
+    # -- poses, weights, state ----------------------------------------------------------------
+    def get_poses(self):
+        R = np.empty((self.n_cams, 3, 3))
+        t = np.empty((self.n_cams, 3))
+        _check(load_library().fm_get_poses(self._h, _ptr(R), _ptr(t)))
+        return R, t
+
+    def set_poses(self, R, t):
+        R = _host(R, np.float64)
+        t = _host(t, np.float64)
+        _check(load_library().fm_set_poses(self._h, _ptr(R), _ptr(t)))
+
+    def get_params(self):
+        """Exact optimiser parameters (R, camera centres c)."""
+        R = np.empty((self.n_cams, 3, 3))
+        c = np.empty((self.n_cams, 3))
+        _check(load_library().fm_get_params(self._h, _ptr(R), _ptr(c)))
+        return R, c
+
+    def set_params(self, R, c):
+        R = _host(R, np.float64)
+        c = _host(c, np.float64)
+        _check(load_library().fm_set_params(self._h, _ptr(R), _ptr(c)))
+
+    def set_weights(self, w):
+        if _is_cuda(w):
+            import torch
+            w = w.to(torch.float32).contiguous()
+            _check(load_library().fm_set_weights(self._h, ctypes.c_void_p(w.data_ptr()), 1))
+        else:
+            wv = _host(w, np.float32)
+            _check(load_library().fm_set_weights(self._h, _ptr(wv), 0))
+
+    def get_weights(self) -> np.ndarray:
+        w = np.empty(self.n_pp, np.float32)
+        _check(load_library().fm_get_weights(self._h, _ptr(w)))
+        return w
+
+    def get_state(self):
+        m = np.empty((self.n_cams, 6))
+        v = np.empty((self.n_cams, 6))
+        s = ctypes.c_int64()
+        _check(load_library().fm_get_state(self._h, _ptr(m), _ptr(v), ctypes.byref(s)))
+        return m, v, s.value
+
+    def set_state(self, m, v, step: int):
+        m = _host(m, np.float64)
+        v = _host(v, np.float64)
+        _check(load_library().fm_set_state(self._h, _ptr(m), _ptr(v), int(step)))
+
+    def reset_optimizer(self):
+        _check(load_library().fm_reset_optimizer(self._h))
+
+    def set_learning_rate(self, lr_rot: float, lr_c: float):
+        _check(load_library().fm_set_learning_rate(self._h, float(lr_rot), float(lr_c)))
+
+    # -- compute -----------------------------------------------------------------------------------
+    def irls_weights(self, tau: float) -> int:
+        n = ctypes.c_int64()
+        _check(load_library().fm_irls_weights(self._h, float(tau), ctypes.byref(n)))
+        return n.value
+
+    def loss_grad(self):
+        loss = ctypes.c_double()
+        g = np.empty((self.n_cams, 6))
+        _check(load_library().fm_loss_grad(self._h, ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def loss_grad_device(self, loss_out, grad_out):
+        """Asynchronous loss/gradient into device tensors (float64, sizes 1 and n_cams*6)."""
+        _check(load_library().fm_loss_grad_device(
+            self._h, ctypes.c_void_p(loss_out.data_ptr()) if loss_out is not None else None,
+            ctypes.c_void_p(grad_out.data_ptr()) if grad_out is not None else None))
+
+    def residuals(self) -> np.ndarray:
+        e = np.empty(self.n_pp, np.float32)
+        _check(load_library().fm_residuals(self._h, _ptr(e)))
+        return e
+
+    def step(self, n_iters: int = 1):
+        _check(load_library().fm_step(self._h, int(n_iters)))
+
+    def last_loss(self) -> float:
+        loss = ctypes.c_double()
+        _check(load_library().fm_last_loss(self._h, ctypes.byref(loss)))
+        return loss.value
+
+    def synchronize(self):
+        _check(load_library().fm_synchronize(self._h))
+
+    def enable_kernel_timing(self, enable: bool = True):
+        _check(load_library().fm_enable_kernel_timing(self._h, 1 if enable else 0))
+
+    def kernel_time(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(load_library().fm_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value

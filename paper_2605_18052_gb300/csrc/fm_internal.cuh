@@ -1,0 +1,108 @@
+// Internal layout and kernel declarations of libfastmap (not part of the C ABI).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "fastmap.h"
+
+namespace fm {
+
+// ---- work decomposition --------------------------------------------------------------------
+// The sorted point-pair array is cut into warp ranges of WR point pairs; each warp streams one
+// range. A range that meets k image pairs produces k partial sums ("slots"). Slot (n, r) of
+// pair n and range r lives at index n + r: along the sorted array every range or pair boundary
+// advances n or r, so n + r is unique per non-empty intersection and there are at most
+// n_pairs + n_ranges slots.
+constexpr int WR = 2048;           // point pairs per warp range
+constexpr int CTA_WARPS = 8;       // warps per CTA of the streaming kernels
+constexpr int SLOT = 12;           // floats per slot: G'(9), loss, 2 pad (48 B)
+constexpr int GEO = 24;            // floats per pair geometry record
+constexpr int CAMREC = 16;         // floats per camera record
+constexpr int PG = 16;             // floats per pair gradient record
+constexpr float COORD_LIMIT = 8.0f;  // |normalized coordinate| bound (fixed-point centroids)
+constexpr int FIXED_SHIFT = 32;    // centroid sums use trunc(x * 2^32) in int64
+
+// geometry record of pair n (written by pair_setup, read by the streaming and combine kernels)
+//   [0..8]  E'_n = T_j^T E_n T_i (centroid-folded essential matrix, row-major)
+//   [9..17] R_n = R_j R_i^T
+//   [18..20] t_n = R_j (c_i - c_j)
+//   [21] 1/|t_n|
+// camera record k (written by the per-camera step kernel)
+//   [0..8] R_k (FP32), [9..11] c_k high part, [12..14] c_k low part (c = hi + lo), [15] 0
+// pair gradient record n: [0..2] g_phi_i, [3..5] g_c_i, [6..8] g_phi_j, [9..11] g_c_j, [12] loss
+
+enum StreamMode { MODE_LOSS_IRLS = 0, MODE_LOSS_L1 = 1 };
+
+enum ErrBits : unsigned {
+    ERR_DEGENERATE = 1u,   // |t_n| == 0 or non-finite pose data
+    ERR_NONFINITE = 2u,    // non-finite loss or gradient
+    ERR_PAIR_RANGE = 4u,   // pair_id out of range
+    ERR_COORD = 8u,        // non-finite or too large keypoint coordinate
+    ERR_EMPTY_PAIR = 16u,  // image pair without point pairs
+    ERR_UNSORTED = 32u,    // input not grouped by pair (not an error: triggers the sort)
+    ERR_WEIGHT = 64u,      // weight outside [0, 1/delta] or non-finite
+};
+
+struct DevProblem {
+    int n_cams, n_pairs;
+    int64_t n_pp;
+    int64_t n_pad;          // allocated point pairs (multiple of WR)
+    int n_ranges;
+    int storage, loss;
+    double delta;
+    float w_scale;          // FP16 weight scale s (1 for FP32 storage)
+    // poses and optimiser state (FP64)
+    double *R, *c, *m, *v, *hyper;   // hyper: lr_rot, lr_c, beta1, beta2, eps
+    long long *step;
+    float *cam;             // camera records
+    float2 *cen;            // per-camera centroids (zeros for FP32 storage)
+    int *cam_i, *cam_j, *pair_off, *range_pair;
+    int *cam_off, *cam_ent;
+    void *kp;               // float4[n_pad] or uint2[n_pad]
+    void *w;                // float[n_pad] or __half[n_pad]
+    int *perm;              // sorted position -> input index, or nullptr (identity)
+    float *geo, *slots, *pair_grad;
+    double *grad, *loss_out;
+    unsigned *err;
+    unsigned long long *counter;
+    float *fbuf;            // n_pad floats of scratch (residual export)
+};
+
+// ---- kernels launched by the API layer (fm_kernels.cu) ----------------------------------------
+void launch_cam_prep(const DevProblem &d, cudaStream_t s);
+void launch_pair_setup(const DevProblem &d, cudaStream_t s);
+void launch_stream_loss(const DevProblem &d, cudaStream_t s);
+void launch_combine(const DevProblem &d, cudaStream_t s);
+void launch_gather(const DevProblem &d, bool count_step, cudaStream_t s);
+void launch_adam(const DevProblem &d, cudaStream_t s);
+void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s);
+void launch_residuals(const DevProblem &d, float *out_sorted, cudaStream_t s);
+
+// ---- layout kernels (fm_layout.cu) -------------------------------------------------------------
+// Validate pair ids / coordinates and detect whether the input is grouped by pair.
+void launch_validate(const int *pair_id, const float2 *x1, const float2 *x2, int64_t n_pp,
+                     int n_pairs, unsigned *err, cudaStream_t s);
+// Stable sort of point pairs by pair id: writes perm (sorted -> input) and sorted keys.
+cudaError_t sort_by_pair(const int *pair_id, int64_t n_pp, int n_pairs, int *keys_out,
+                         int *perm_out, cudaStream_t s);
+void launch_pair_offsets(const int *sorted_keys, int64_t n_pp, int n_pairs, int *pair_off,
+                         unsigned *err, cudaStream_t s);
+void launch_range_pairs(const int *pair_off, int n_pairs, int n_ranges, int *range_pair,
+                        cudaStream_t s);
+// FP16 storage: per-image centroids into d.cen (needs d.cam_off/cam_ent/pair_off/perm);
+// `sums` is scratch for 2 * n_cams int64.
+void launch_centroids(const DevProblem &d, const int *sorted_keys, const float2 *x1,
+                      const float2 *x2, unsigned long long *sums, cudaStream_t s);
+void launch_pack(const DevProblem &d, const int *sorted_keys, const float2 *x1, const float2 *x2,
+                 cudaStream_t s);
+void launch_fill_weights(const DevProblem &d, float value, cudaStream_t s);
+void launch_set_weights(const DevProblem &d, const float *w_input_order, cudaStream_t s);
+void launch_get_weights(const DevProblem &d, float *w_input_order, cudaStream_t s);
+void launch_unpermute(const DevProblem &d, const float *sorted, float *input_order,
+                      cudaStream_t s);
+
+}  // namespace fm

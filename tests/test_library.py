@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for sm_103a, loads, and
+exports every entry point include/fastmap.h declares; the binding rejects bad arguments
+before any device work."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_2605_18052_gb300 as fm
+from paper_2605_18052_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "fastmap.h")).read()
+    return sorted(set(re.findall(r"FM_API[^;(]*?\b(fm_\w+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["fm_create_problem", "fm_loss_grad", "fm_irls_weights", "fm_step", "fm_get_poses",
+              "fm_destroy_problem", "fm_last_error"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (fm_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    # and the binding knows every one of them
+    assert sorted(binding.EXPORTED) == _declared()
+    for n in _declared():
+        getattr(lib, n)
+
+
+def test_build_flags_target_sm_103a():
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_default_options(lib):
+    o = fm.default_options()
+    assert (o.storage, o.loss, o.delta, o.beta1, o.beta2, o.use_graph) == (0, 0, 1e-6, 0.9, 0.999, 1)
+    o = fm.default_options(storage="fp16", loss="l1")
+    assert (o.storage, o.loss) == (fm.FM_STORE_FP16, fm.FM_LOSS_L1)
+
+
+def test_create_rejects_bad_host_arguments_without_a_gpu(lib):
+    # validation of host-side arguments happens before any CUDA call
+    R = np.tile(np.eye(3), (2, 1, 1))
+    t = np.array([[0.0, 0, 0], [1.0, 0, 0]])
+    x = np.zeros((3, 2), np.float32)
+    pid = np.zeros(3, np.int32)
+    cases = [
+        dict(R=R[:1], t=t[:1], cam_i=[0], cam_j=[1]),            # n_cams < 2
+        dict(R=R, t=t, cam_i=[0], cam_j=[0]),                    # cam_i == cam_j
+        dict(R=R, t=t, cam_i=[0], cam_j=[2]),                    # camera index out of range
+        dict(R=R, t=t, cam_i=[0, 1], cam_j=[1, 0], pid=np.zeros(1, np.int32), xx=np.zeros((1, 2), np.float32)),
+    ]
+    for c in cases:
+        with pytest.raises(fm.FastMapError) as ei:
+            fm.Problem(c["R"], c["t"], c["cam_i"], c["cam_j"], c.get("pid", pid), c.get("xx", x),
+                       c.get("xx", x))
+        assert ei.value.status == -1
+    with pytest.raises(fm.FastMapError):
+        fm.Problem(R, t, [0], [1], pid, x, x, options=fm.default_options(delta=0.0))
+    with pytest.raises(fm.FastMapError):
+        fm.Problem(R, t, [0], [1], pid, x, x, options=fm.default_options(beta1=1.0))
