@@ -215,6 +215,7 @@ def main():
 
     # each rank: its own seeded scene (weak scaling: replicas, no data-path collective)
     sc = scenegen.make_scene(args.config, seed=args.seed + rank, device="cuda")
+    torch.cuda.empty_cache()   # drop the generator's temporaries
     sch = schedule_for(sc, args.iters)
     opt = fm.default_options(storage=args.storage, lr_rot=sch.lr_rot, lr_c=sch.lr_c)
     stream = torch.cuda.current_stream()

@@ -347,8 +347,14 @@ __global__ void k_pair_setup(DevProblem d) {
         tn[a] = Rj[3 * a] * dc[0] + Rj[3 * a + 1] * dc[1] + Rj[3 * a + 2] * dc[2];
     }
     const float nt2 = tn[0] * tn[0] + tn[1] * tn[1] + tn[2] * tn[2];
+    // a baseline below 1e-10 of the centres' magnitude is rounding noise: its direction,
+    // and so E_n, is undefined
+    float cmax = 1.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cmax = fmaxf(cmax, fmaxf(fabsf(ci[9 + q]), fabsf(cj[9 + q])));
+    const float floor2 = 1e-20f * cmax * cmax;
     float inv = 0.f;
-    if (nt2 > 1e-36f && isfinite(nt2)) {
+    if (nt2 > floor2 && isfinite(nt2)) {
         inv = 1.0f / sqrtf(nt2);
     } else {
         atomicOr(d.err, ERR_DEGENERATE);
