@@ -209,6 +209,39 @@ FM_API fm_status fm_synchronize(fm_problem *p);
 FM_API fm_status fm_enable_kernel_timing(fm_problem *p, int32_t enable);
 FM_API fm_status fm_kernel_time(fm_problem *p, double *ms, int64_t *launches);
 
+/*
+ * Loss and gradient without any device allocation, for callers that cannot call cudaMalloc:
+ * code whose device memory is owned by another memory manager (a framework's caching
+ * allocator, a fixed arena), or a loop that cannot afford cudaMalloc's implicit device
+ * synchronisation. The paper has no counterpart; this is an interface convenience that
+ * computes the same quantities as fm_loss_grad.
+ *
+ * All pointers are device pointers the caller owns:
+ *   d_R (n_cams x 9 FP64) rotations and d_c (n_cams x 3 FP64) camera centres c = -R^T t;
+ *   d_cam_i, d_cam_j (n_pairs int32) image pairs; d_pair_off (n_pairs + 1 int32) offsets of
+ *   each pair's point pairs, rising strictly from 0 to n_pp (point pairs sorted by pair);
+ *   d_kp (n_pp x 4 FP32, 16-byte aligned) rows (x1, y1, x2, y2) in normalized coordinates;
+ *   d_w (n_pp FP32) IRLS weights, or NULL for all ones (ignored when loss is FM_LOSS_L1);
+ *   outputs d_loss (1 FP64) and d_grad (n_cams x 6 FP64, ordered as for fm_loss_grad).
+ * Limits: 2 <= n_cams <= 4096, 1 <= n_pairs <= 32768, n_pairs <= n_pp <= 2^26; larger
+ * problems return FM_EINVAL (use fm_create_problem for them).
+ *
+ * Intermediates live in one fixed 9.3 MiB __device__ array of the library, held on every
+ * device that loads it until the process exits. The first call on a device looks up the
+ * array's device address with that device current; make that first call before any stream
+ * capture. Every call shares the array, so calls that overlap on the GPU (other streams,
+ * other host threads on the same device) race and must be serialised by the caller.
+ * Runs on `stream` (a cudaStream_t, NULL = legacy default) and synchronises it before
+ * returning. Invalid device data (offsets not rising, camera index out of range,
+ * cam_i == cam_j) returns FM_EINVAL; a zero-length relative translation or a non-finite
+ * result returns FM_EDEGENERATE.
+ */
+FM_API fm_status fm_loss_grad_noalloc(int32_t n_cams, const double *d_R, const double *d_c,
+                                      int32_t n_pairs, const int32_t *d_cam_i,
+                                      const int32_t *d_cam_j, const int32_t *d_pair_off,
+                                      int64_t n_pp, const float *d_kp, const float *d_w,
+                                      int32_t loss, double *d_loss, double *d_grad, void *stream);
+
 FM_API const char *fm_status_string(fm_status s);
 FM_API const char *fm_last_error(void);
 

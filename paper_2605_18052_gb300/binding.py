@@ -21,8 +21,8 @@ EXPORTED = [
     "fm_get_poses", "fm_set_poses", "fm_get_params", "fm_set_params", "fm_set_weights", "fm_get_weights", "fm_irls_weights",
     "fm_loss_grad", "fm_loss_grad_device", "fm_residuals", "fm_step", "fm_last_loss",
     "fm_set_learning_rate", "fm_reset_optimizer", "fm_get_state", "fm_set_state",
-    "fm_synchronize", "fm_enable_kernel_timing", "fm_kernel_time", "fm_status_string",
-    "fm_last_error",
+    "fm_synchronize", "fm_enable_kernel_timing", "fm_kernel_time", "fm_loss_grad_noalloc",
+    "fm_status_string", "fm_last_error",
 ]
 
 
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "fm_synchronize": (I32, [P]),
         "fm_enable_kernel_timing": (I32, [P, I32]),
         "fm_kernel_time": (I32, [P, P, P]),
+        "fm_loss_grad_noalloc": (I32, [I32, P, P, I32, P, P, P, I64, P, P, I32, P, P, P]),
         "fm_status_string": (ctypes.c_char_p, [I32]),
         "fm_last_error": (ctypes.c_char_p, []),
     }

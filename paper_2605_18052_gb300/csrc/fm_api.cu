@@ -32,6 +32,9 @@ fm_status fail(fm_status s, const std::string &msg) {
 
 }  // namespace
 
+// lets other translation units of the library report through fm_last_error
+void fm_internal_set_error(const char *msg) { g_last_error = msg; }
+
 struct fm_problem {
     DevProblem d{};
     fm_options opt{};

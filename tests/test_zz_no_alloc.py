@@ -1,0 +1,106 @@
+"""fm_loss_grad_noalloc: loss and gradient for callers that cannot call cudaMalloc (device
+memory owned by another memory manager, or a loop that cannot afford cudaMalloc's implicit
+device synchronisation). Its intermediates live in a fixed __device__ array of the library.
+
+Checked through the C ABI against the existing entry point (fm_create_problem +
+fm_loss_grad) with the parity tolerance used for the oracle (loss relative 1e-4, gradient
+within 1e-4 of its largest entry), on two calls in a row of different sizes (stale scratch
+from the first call must not leak into the second), plus: a repeated call is bit-identical,
+device free memory does not change across a call, and sizes beyond the limits are refused.
+This file is collected last so a run that stops at the first failure has run everything else.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import scenegen
+import paper_2605_18052_gb300 as fm
+from paper_2605_18052_gb300 import binding, build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    build.build()
+    return binding.load_library()
+
+
+def _inputs(sc, mode, seed):
+    rng = np.random.default_rng(seed)
+    R = sc.R_init.numpy()
+    t = sc.t_init.numpy()
+    w = rng.uniform(0.0, 20.0, sc.n_pp).astype(np.float32)
+    dev = torch.device("cuda")
+    c = -np.einsum("nba,nb->na", R, t)
+    pid = sc.pair_id.long()
+    off = torch.zeros(sc.n_pairs + 1, dtype=torch.int32)
+    off[1:] = torch.cumsum(torch.bincount(pid, minlength=sc.n_pairs), 0).to(torch.int32)
+    d = {
+        "R": torch.as_tensor(R.reshape(-1, 9), dtype=torch.float64, device=dev).contiguous(),
+        "c": torch.as_tensor(c, dtype=torch.float64, device=dev).contiguous(),
+        "ci": sc.cam_i.to(dev).contiguous(), "cj": sc.cam_j.to(dev).contiguous(),
+        "off": off.to(dev), "kp": torch.cat([sc.x1, sc.x2], 1).to(dev).contiguous(),
+        "w": torch.as_tensor(w, device=dev), "loss": torch.zeros(1, dtype=torch.float64, device=dev),
+        "grad": torch.zeros(sc.n_cams * 6, dtype=torch.float64, device=dev),
+    }
+    return R, t, w, d
+
+
+def _call(lib, sc, d, mode):
+    P = lambda x: ctypes.c_void_p(x.data_ptr())
+    st = lib.fm_loss_grad_noalloc(sc.n_cams, P(d["R"]), P(d["c"]), sc.n_pairs, P(d["ci"]), P(d["cj"]),
+                                  P(d["off"]), sc.n_pp, P(d["kp"]), P(d["w"]), mode, P(d["loss"]),
+                                  P(d["grad"]), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, lib.fm_last_error().decode()
+    return float(d["loss"].item()), d["grad"].cpu().numpy().reshape(-1, 6)
+
+
+def _reference(sc, R, t, w, mode):
+    with fm.Problem(R, t, sc.cam_i, sc.cam_j, sc.pair_id, sc.x1, sc.x2,
+                    options=fm.default_options(loss=mode)) as gp:
+        if mode == fm.FM_LOSS_IRLS:
+            gp.set_weights(w)
+        return gp.loss_grad()
+
+
+def _close(l, g, l_ref, g_ref):
+    assert l == pytest.approx(l_ref, rel=1e-4)
+    assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
+
+
+def test_noalloc_matches_loss_grad_on_two_calls(lib):
+    big = scenegen.make_scene("sphere128", seed=3)
+    small = scenegen.make_scene("ring16", seed=4)
+    R1, t1, w1, d1 = _inputs(big, fm.FM_LOSS_IRLS, 1)
+    R2, t2, w2, d2 = _inputs(small, fm.FM_LOSS_L1, 2)
+    ref1 = _reference(big, R1, t1, w1, fm.FM_LOSS_IRLS)
+    ref2 = _reference(small, R2, t2, w2, fm.FM_LOSS_L1)
+    torch.cuda.synchronize()
+
+    l1, g1 = _call(lib, big, d1, fm.FM_LOSS_IRLS)        # first call on this device
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    l2, g2 = _call(lib, small, d2, fm.FM_LOSS_L1)        # second call, smaller problem
+    torch.cuda.synchronize()
+    free_after = torch.cuda.mem_get_info()[0]
+    _close(l1, g1, *ref1)
+    _close(l2, g2, *ref2)
+    assert free_after == free_before
+
+    l3, g3 = _call(lib, small, d2, fm.FM_LOSS_L1)        # same inputs again: same bits
+    assert l3 == l2
+    np.testing.assert_array_equal(g3, g2)
+
+
+def test_noalloc_refuses_sizes_beyond_its_limits(lib):
+    z = ctypes.c_void_p(16)   # never dereferenced: sizes are checked first
+    cases = [(4097, 10, 100), (2, 32769, 40000), (2, 1, (1 << 26) + 1), (1, 1, 1)]
+    for n_cams, n_pairs, n_pp in cases:
+        st = lib.fm_loss_grad_noalloc(n_cams, z, z, n_pairs, z, z, z, n_pp, z, None, 0, z, z, None)
+        assert st == -1
+        assert "fm_loss_grad_noalloc" in lib.fm_last_error().decode()
