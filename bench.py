@@ -231,22 +231,28 @@ def main():
     for r in range(args.warmup):
         one_step(r)
     gp.synchronize()
-    gp.enable_kernel_timing(True)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        # timed region: the production path (CUDA graphs of chained iterations)
         torch.cuda.synchronize()
         ev0.record(stream)
         for k in range(args.steps):
             one_step(args.warmup + k)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    kern_ms, kern_n = gp.kernel_time()
-    gp.enable_kernel_timing(False)
+        ms = ev0.elapsed_time(ev1)
+        # second timed region, same steps, with CUDA events around every launch of the
+        # streaming kernel on the problem's stream (eager launches): its mean duration
+        gp.enable_kernel_timing(True)
+        for k in range(args.steps):
+            one_step(args.warmup + args.steps + k)
+        kern_ms, kern_n = gp.kernel_time()
+        gp.enable_kernel_timing(False)
+        torch.cuda.synchronize()
     t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
     pp_local = torch.tensor([float(n_pp) * args.iters * args.steps], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -267,7 +273,7 @@ def main():
                 "kernel": f"k_stream_loss<{args.storage.upper()}, IRLS>",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs burst copy)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6}
-    launches = args.steps * (2 + 5 * args.iters)
+    launches = args.steps * (2 + 3 * args.iters)
     clocks = clk.summary()
 
     # end to end through the public API with pinned host buffers: create + full schedule + poses
@@ -278,21 +284,27 @@ def main():
         cih, cjh = sc.cam_i.cpu(), sc.cam_j.cpu()
         del gp
         torch.cuda.synchronize()
-        times = []
+        times, parts = [], []
         for k in range(3):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with fm.Problem(Rh, th, cih, cjh, h["pair_id"], h["x1"], h["x2"], options=opt) as jp:
-                fm.refine(jp, sch)
-                R_out, t_out = jp.get_poses()
-            times.append(time.perf_counter() - t0)
+            jp = fm.Problem(Rh, th, cih, cjh, h["pair_id"], h["x1"], h["x2"], options=opt)
+            t1 = time.perf_counter()
+            fm.refine(jp, sch)
+            R_out, t_out = jp.get_poses()
+            t2 = time.perf_counter()
+            jp.close()
+            t3 = time.perf_counter()
+            times.append(t3 - t0)
+            parts.append((t1 - t0, t2 - t1, t3 - t2))
         t_job = statistics.median(times[1:])
         e2e_pp = float(n_pp) * sch.rounds * sch.iters_per_round
         e2e = {"value": e2e_pp / t_job / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(n_pp * (4 + 8 + 8) + sc.n_cams * 12 * 8 + sc.n_pairs * 8),
                "d2h_bytes_per_step": int(sc.n_cams * 12 * 8),
                "job": f"fm_create_problem from pinned host buffers + {sch.rounds} rounds x {sch.iters_per_round} iterations + fm_get_poses",
-               "seconds_per_job": t_job}
+               "seconds_per_job": t_job,
+               "seconds_create_refine_destroy": [round(statistics.median(x[i] for x in parts[1:]), 5) for i in range(3)]}
 
     cpu = None
     if rank == 0 and not args.no_cpu:

@@ -175,7 +175,8 @@ FM_API fm_status fm_residuals(fm_problem *p, float *eps);
 
 /*
  * n_iters optimiser iterations, each: objective gradient at the current poses, one Adam
- * step on (phi_k, c_k), R_k <- Exp(phi_k) R_k with FP64 re-orthonormalisation. Only
+ * step on (phi_k, c_k) (FP32 moments), R_k <- Exp(phi_k) R_k with FP64 exponential map and
+ * re-orthonormalisation, c_k updated in FP64. Only
  * enqueues work; errors found on the device surface at the next synchronising call.
  */
 FM_API fm_status fm_step(fm_problem *p, int32_t n_iters);
@@ -190,8 +191,9 @@ FM_API fm_status fm_set_learning_rate(fm_problem *p, double lr_rot, double lr_c)
 FM_API fm_status fm_reset_optimizer(fm_problem *p);
 
 /*
- * Optimiser state for checkpoint/resume: m and v (n_cams x 6 FP64 each, host) and the
- * 1-based number of Adam steps taken. Resuming from a saved (poses, weights, state) gives
+ * Optimiser state for checkpoint/resume: m and v (n_cams x 6, host FP64 arrays; the device
+ * keeps them in FP32, so values round-trip exactly when they came from fm_get_state) and the
+ * number of Adam steps taken. Resuming from a saved (poses, weights, state) gives
  * bit-identical trajectories because every reduction runs in a fixed order.
  */
 FM_API fm_status fm_get_state(fm_problem *p, double *m, double *v, int64_t *step);
@@ -226,7 +228,7 @@ FM_API fm_status fm_kernel_time(fm_problem *p, double *ms, int64_t *launches);
  * Limits: 2 <= n_cams <= 4096, 1 <= n_pairs <= 32768, n_pairs <= n_pp <= 2^26; larger
  * problems return FM_EINVAL (use fm_create_problem for them).
  *
- * Intermediates live in one fixed 9.3 MiB __device__ array of the library, held on every
+ * Intermediates live in one fixed 10.2 MiB __device__ array of the library, held on every
  * device that loads it until the process exits. The first call on a device looks up the
  * array's device address with that device current; make that first call before any stream
  * capture. Every call shares the array, so calls that overlap on the GPU (other streams,

@@ -41,7 +41,8 @@ struct fm_problem {
     cudaStream_t user = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;      // one iteration
+    cudaGraphExec_t graph8 = nullptr;     // eight chained iterations
     bool timing = false;
     std::vector<cudaEvent_t> tev;   // timing events, pairs (start, end)
     size_t tev_used = 0;
@@ -147,9 +148,10 @@ fm_status check_options(const fm_options *o) {
     return FM_OK;
 }
 
-// one optimiser iteration (five launches)
-void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed) {
-    launch_pair_setup(p->d, s);
+// one optimiser iteration (three launches, chained with programmatic dependent launch);
+// `first` = the iteration does not follow another one in this chain
+void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed, bool first) {
+    launch_pair_setup(p->d, s, true, !first);
     if (timed) {
         if (p->tev_used + 2 > p->tev.size()) {
             for (int k = 0; k < 64; ++k) {
@@ -159,27 +161,33 @@ void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed) {
             }
         }
         cudaEventRecord(p->tev[p->tev_used], s);
-        launch_stream_loss(p->d, s);
+        launch_stream_loss(p->d, s, false);
         cudaEventRecord(p->tev[p->tev_used + 1], s);
         p->tev_used += 2;
+        launch_camera_step(p->d, true, s, false);
     } else {
-        launch_stream_loss(p->d, s);
+        launch_stream_loss(p->d, s, true);
+        launch_camera_step(p->d, true, s, true);
     }
-    launch_combine(p->d, s);
-    launch_gather(p->d, true, s);
-    launch_adam(p->d, s);
 }
 
-fm_status build_graph(fm_problem *p) {
+// `iters` chained iterations and the closing finalize launch
+void enqueue_iterations(fm_problem *p, cudaStream_t s, bool timed, int iters) {
+    for (int it = 0; it < iters; ++it) enqueue_iteration(p, s, timed, it == 0);
+    launch_finalize(p->d, true, s, !timed);
+}
+
+// a graph of `iters` chained iterations
+fm_status build_graph(fm_problem *p, int iters, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     FM_CUDA(cudaStreamBeginCapture(p->s, cudaStreamCaptureModeThreadLocal));
-    enqueue_iteration(p, p->s, false);
+    enqueue_iterations(p, p->s, false, iters);
     cudaError_t e = cudaStreamEndCapture(p->s, &g);
     if (e != cudaSuccess) return fail(FM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&p->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        p->graph = nullptr;
+        *out = nullptr;
         return fail(FM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
     return FM_OK;
@@ -190,6 +198,7 @@ void free_problem(fm_problem *p) {
     if (p->s) cudaStreamSynchronize(p->s);
     for (void *a : p->allocs) cudaFree(a);
     if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->graph8) cudaGraphExecDestroy(p->graph8);
     for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
@@ -237,6 +246,7 @@ fm_status create_impl(fm_problem *p, int32_t n_cams, const double *R, const doub
     FM_CUDA(dalloc(p, &d.c, 3 * (size_t)n_cams));
     FM_CUDA(dalloc(p, &d.m, 6 * (size_t)n_cams));
     FM_CUDA(dalloc(p, &d.v, 6 * (size_t)n_cams));
+    FM_CUDA(dalloc(p, &d.cam_loss, (size_t)camera_step_blocks(d)));
     FM_CUDA(dalloc(p, &d.hyper, 8));
     FM_CUDA(dalloc(p, &d.step, 1));
     FM_CUDA(dalloc(p, &d.cam, (size_t)CAMREC * n_cams));
@@ -273,8 +283,8 @@ fm_status create_impl(fm_problem *p, int32_t n_cams, const double *R, const doub
     d.fbuf = nullptr;
 
     FM_CUDA(cudaMemsetAsync(d.err, 0, sizeof(unsigned), p->s));
-    FM_CUDA(cudaMemsetAsync(d.m, 0, sizeof(double) * 6 * n_cams, p->s));
-    FM_CUDA(cudaMemsetAsync(d.v, 0, sizeof(double) * 6 * n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(d.m, 0, sizeof(float) * 6 * n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(d.v, 0, sizeof(float) * 6 * n_cams, p->s));
     FM_CUDA(cudaMemsetAsync(d.step, 0, sizeof(long long), p->s));
     FM_CUDA(cudaMemsetAsync(d.cen, 0, sizeof(float2) * n_cams, p->s));
     FM_CUDA(cudaMemsetAsync(d.geo, 0, sizeof(float) * GEO * n_pairs, p->s));
@@ -561,8 +571,8 @@ FM_API fm_status fm_loss_grad_device(fm_problem *p, double *d_loss, double *d_gr
     FM_CUDA(join_in(p));
     launch_pair_setup(p->d, p->s);
     launch_stream_loss(p->d, p->s);
-    launch_combine(p->d, p->s);
-    launch_gather(p->d, false, p->s);
+    launch_camera_step(p->d, false, p->s);
+    launch_finalize(p->d, false, p->s);
     FM_CUDA(cudaGetLastError());
     if (d_loss) FM_CUDA(cudaMemcpyAsync(d_loss, p->d.loss_out, sizeof(double), cudaMemcpyDeviceToDevice, p->s));
     if (d_grad)
@@ -577,8 +587,8 @@ FM_API fm_status fm_loss_grad(fm_problem *p, double *loss, double *grad) {
     FM_CUDA(join_in(p));
     launch_pair_setup(p->d, p->s);
     launch_stream_loss(p->d, p->s);
-    launch_combine(p->d, p->s);
-    launch_gather(p->d, false, p->s);
+    launch_camera_step(p->d, false, p->s);
+    launch_finalize(p->d, false, p->s);
     FM_CUDA(cudaGetLastError());
     FM_CUDA(cudaMemcpyAsync(loss, p->d.loss_out, sizeof(double), cudaMemcpyDeviceToHost, p->s));
     if (grad)
@@ -609,14 +619,20 @@ FM_API fm_status fm_step(fm_problem *p, int32_t n_iters) {
     if (n_iters == 0) return FM_OK;
     FM_CUDA(join_in(p));
     if (p->timing || !p->opt.use_graph) {
-        for (int it = 0; it < n_iters; ++it) enqueue_iteration(p, p->s, p->timing);
+        enqueue_iterations(p, p->s, p->timing, n_iters);
         FM_CUDA(cudaGetLastError());
     } else {
         if (!p->graph) {
-            fm_status st = build_graph(p);
+            fm_status st = build_graph(p, 1, &p->graph);
             if (st != FM_OK) return st;
         }
-        for (int it = 0; it < n_iters; ++it) FM_CUDA(cudaGraphLaunch(p->graph, p->s));
+        if (n_iters >= 8 && !p->graph8) {
+            fm_status st = build_graph(p, 8, &p->graph8);
+            if (st != FM_OK) return st;
+        }
+        int left = n_iters;
+        for (; left >= 8; left -= 8) FM_CUDA(cudaGraphLaunch(p->graph8, p->s));
+        for (; left > 0; --left) FM_CUDA(cudaGraphLaunch(p->graph, p->s));
     }
     FM_CUDA(join_out(p));
     return FM_OK;
@@ -643,8 +659,8 @@ FM_API fm_status fm_set_learning_rate(fm_problem *p, double lr_rot, double lr_c)
 FM_API fm_status fm_reset_optimizer(fm_problem *p) {
     if (fm_status st = check_problem(p)) return st;
     FM_CUDA(join_in(p));
-    FM_CUDA(cudaMemsetAsync(p->d.m, 0, sizeof(double) * 6 * p->d.n_cams, p->s));
-    FM_CUDA(cudaMemsetAsync(p->d.v, 0, sizeof(double) * 6 * p->d.n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(p->d.m, 0, sizeof(float) * 6 * p->d.n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(p->d.v, 0, sizeof(float) * 6 * p->d.n_cams, p->s));
     FM_CUDA(cudaMemsetAsync(p->d.step, 0, sizeof(long long), p->s));
     FM_CUDA(cudaStreamSynchronize(p->s));
     return FM_OK;
@@ -654,11 +670,17 @@ FM_API fm_status fm_get_state(fm_problem *p, double *m, double *v, int64_t *step
     if (fm_status st = check_problem(p)) return st;
     if (!m || !v || !step) return fail(FM_EINVAL, "m, v and step must not be NULL");
     long long s = 0;
+    const size_t n6 = 6 * (size_t)p->d.n_cams;
+    std::vector<float> mf(n6), vf(n6);
     FM_CUDA(join_in(p));
-    FM_CUDA(cudaMemcpyAsync(m, p->d.m, sizeof(double) * 6 * p->d.n_cams, cudaMemcpyDeviceToHost, p->s));
-    FM_CUDA(cudaMemcpyAsync(v, p->d.v, sizeof(double) * 6 * p->d.n_cams, cudaMemcpyDeviceToHost, p->s));
+    FM_CUDA(cudaMemcpyAsync(mf.data(), p->d.m, sizeof(float) * n6, cudaMemcpyDeviceToHost, p->s));
+    FM_CUDA(cudaMemcpyAsync(vf.data(), p->d.v, sizeof(float) * n6, cudaMemcpyDeviceToHost, p->s));
     FM_CUDA(cudaMemcpyAsync(&s, p->d.step, sizeof s, cudaMemcpyDeviceToHost, p->s));
     FM_CUDA(cudaStreamSynchronize(p->s));
+    for (size_t k = 0; k < n6; ++k) {
+        m[k] = mf[k];
+        v[k] = vf[k];
+    }
     *step = s;
     return FM_OK;
 }
@@ -672,9 +694,15 @@ FM_API fm_status fm_set_state(fm_problem *p, const double *m, const double *v, i
     for (size_t k = 0; k < 6 * (size_t)p->d.n_cams; ++k)
         if (v[k] < 0.0) return fail(FM_EINVAL, "second moments must be >= 0");
     const long long s = step;
+    const size_t n6 = 6 * (size_t)p->d.n_cams;
+    std::vector<float> mf(n6), vf(n6);
+    for (size_t k = 0; k < n6; ++k) {
+        mf[k] = (float)m[k];
+        vf[k] = (float)v[k];
+    }
     FM_CUDA(join_in(p));
-    FM_CUDA(cudaMemcpyAsync(p->d.m, m, sizeof(double) * 6 * p->d.n_cams, cudaMemcpyHostToDevice, p->s));
-    FM_CUDA(cudaMemcpyAsync(p->d.v, v, sizeof(double) * 6 * p->d.n_cams, cudaMemcpyHostToDevice, p->s));
+    FM_CUDA(cudaMemcpyAsync(p->d.m, mf.data(), sizeof(float) * n6, cudaMemcpyHostToDevice, p->s));
+    FM_CUDA(cudaMemcpyAsync(p->d.v, vf.data(), sizeof(float) * n6, cudaMemcpyHostToDevice, p->s));
     FM_CUDA(cudaMemcpyAsync(p->d.step, &s, sizeof s, cudaMemcpyHostToDevice, p->s));
     FM_CUDA(cudaStreamSynchronize(p->s));
     return FM_OK;

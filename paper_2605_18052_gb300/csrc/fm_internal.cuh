@@ -20,7 +20,7 @@ namespace fm {
 constexpr int WR = 2048;           // point pairs per warp range
 constexpr int CTA_WARPS = 8;       // warps per CTA of the streaming kernels
 constexpr int SLOT = 12;           // floats per slot: G'(9), loss, 2 pad (48 B)
-constexpr int GEO = 24;            // floats per pair geometry record
+constexpr int GEO = 36;            // floats per pair geometry record (144 B)
 constexpr int CAMREC = 16;         // floats per camera record
 constexpr int PG = 16;             // floats per pair gradient record
 constexpr float COORD_LIMIT = 8.0f;  // |normalized coordinate| bound (fixed-point centroids)
@@ -30,7 +30,9 @@ constexpr int FIXED_SHIFT = 32;    // centroid sums use trunc(x * 2^32) in int64
 //   [0..8]  E'_n = T_j^T E_n T_i (centroid-folded essential matrix, row-major)
 //   [9..17] R_n = R_j R_i^T
 //   [18..20] t_n = R_j (c_i - c_j)
-//   [21] 1/|t_n|
+//   [21] 1/|t_n|, [22..23] centroid of image i, [33..34] centroid of image j
+//   [24..32] R_j (the second camera's rotation, so the per-camera step never reads another
+//            camera's record while that record is being updated)
 // camera record k (written by the per-camera step kernel)
 //   [0..8] R_k (FP32), [9..11] c_k high part, [12..14] c_k low part (c = hi + lo), [15] 0
 // pair gradient record n: [0..2] g_phi_i, [3..5] g_c_i, [6..8] g_phi_j, [9..11] g_c_j, [12] loss
@@ -55,9 +57,11 @@ struct DevProblem {
     int storage, loss;
     double delta;
     float w_scale;          // FP16 weight scale s (1 for FP32 storage)
-    // poses and optimiser state (FP64)
-    double *R, *c, *m, *v, *hyper;   // hyper: lr_rot, lr_c, beta1, beta2, eps
+    // poses (FP64) and Adam moments (FP32)
+    double *R, *c, *hyper;   // hyper: lr_rot, lr_c, beta1, beta2, eps
+    float *m, *v;
     long long *step;
+    double *cam_loss;        // per-block loss partials of the fused step kernel
     float *cam;             // camera records
     float2 *cen;            // per-camera centroids (zeros for FP32 storage)
     int *cam_i, *cam_j, *pair_off, *range_pair;
@@ -74,11 +78,21 @@ struct DevProblem {
 
 // ---- kernels launched by the API layer (fm_kernels.cu) ----------------------------------------
 void launch_cam_prep(const DevProblem &d, cudaStream_t s);
-void launch_pair_setup(const DevProblem &d, cudaStream_t s);
-void launch_stream_loss(const DevProblem &d, cudaStream_t s);
+// pdl: launch with programmatic stream serialisation (overlaps the predecessor's tail)
+// after_step: the previous kernel was an optimiser camera step whose loss total and step
+// count this launch finishes
+void launch_pair_setup(const DevProblem &d, cudaStream_t s, bool pdl = false, bool after_step = false);
+// loss total of the last camera step (and the step count after an optimiser step)
+void launch_finalize(const DevProblem &d, bool count_step, cudaStream_t s, bool pdl = false);
+int camera_step_blocks(const DevProblem &d);
+// streaming loss + adjoint: per (image pair, CTA range) partial sums in d.slots
+void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl = false);
 void launch_combine(const DevProblem &d, cudaStream_t s);
 void launch_gather(const DevProblem &d, bool count_step, cudaStream_t s);
-void launch_adam(const DevProblem &d, cudaStream_t s);
+// fused per-camera step: combine this camera's pair partials, chain rule, FP64 sum, Adam,
+// exponential map, camera record; the last block sums the loss and advances the step count
+// apply = false computes the gradient and loss only (no Adam step, no step count)
+void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl = false);
 void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s);
 void launch_residuals(const DevProblem &d, float *out_sorted, cudaStream_t s);
 
@@ -93,7 +107,7 @@ void launch_pair_offsets(const int *sorted_keys, int64_t n_pp, int n_pairs, int 
                          unsigned *err, cudaStream_t s);
 void launch_range_pairs(const int *pair_off, int n_pairs, int n_ranges, int *range_pair,
                         cudaStream_t s);
-// FP16 storage: per-image centroids into d.cen (needs d.cam_off/cam_ent/pair_off/perm);
+// FP16 storage: per-image centroids into d.cen (needs d.cam_off/cam_ent/pair_off/range_pair/perm);
 // `sums` is scratch for 2 * n_cams int64.
 void launch_centroids(const DevProblem &d, const int *sorted_keys, const float2 *x1,
                       const float2 *x2, unsigned long long *sums, cudaStream_t s);

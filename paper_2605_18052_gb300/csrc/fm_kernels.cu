@@ -15,18 +15,53 @@
 
 namespace fm {
 
-// ---- streaming loads: 16 B vectors, no L1 allocation, 256 B L2 prefetch -----------------------
-__device__ __forceinline__ uint4 ld_stream_v4(const void *p) {
+// ---- programmatic dependent launch --------------------------------------------------------------
+// The three kernels of an optimiser iteration are launched with programmatic stream
+// serialisation, so a kernel's CTAs can be scheduled while its predecessor drains. Every kernel
+// waits (griddepcontrol.wait) before it reads anything its predecessor writes, and lets its own
+// dependents launch (griddepcontrol.launch_dependents) only after that wait: when a kernel
+// starts, the kernel two places before it has completed, so reads of older data before the
+// wait are safe. Both instructions are no-ops for a normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                            bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// ---- streaming loads: 16 B vectors, no L1 allocation, evict-first in L2 -----------------------
+// The point-pair arrays are read once per pass and are 10-100x larger than L2; marking them
+// evict-first keeps the small per-pair and per-camera tables (geometry, partial sums, camera
+// lists, poses) resident in L2 across passes, which the latency-bound per-camera step needs.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ uint4 ld_stream_v4(const void *p, uint64_t pol) {
     uint4 r;
-    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
         : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(p));
+        : "l"(p), "l"(pol));
     return r;
 }
 
-__device__ __forceinline__ unsigned ld_stream_u32(const void *p) {
+__device__ __forceinline__ unsigned ld_stream_u32(const void *p, uint64_t pol) {
     unsigned r;
-    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
     return r;
 }
 
@@ -42,10 +77,10 @@ struct Fmt<FM_STORE_FP32> {
         uint4 kp;
         unsigned w;
     };
-    __device__ static Raw load(const DevProblem &d, int64_t q, bool need_w) {
+    __device__ static Raw load(const DevProblem &d, int64_t q, bool need_w, uint64_t pol) {
         Raw r;
-        r.kp = ld_stream_v4(static_cast<const float4 *>(d.kp) + q);
-        r.w = need_w ? ld_stream_u32(static_cast<const float *>(d.w) + q) : 0u;
+        r.kp = ld_stream_v4(static_cast<const float4 *>(d.kp) + q, pol);
+        r.w = need_w ? ld_stream_u32(static_cast<const float *>(d.w) + q, pol) : 0u;
         return r;
     }
     __device__ static void get(const Raw &r, int, float &x1, float &y1, float &x2, float &y2,
@@ -67,10 +102,10 @@ struct Fmt<FM_STORE_FP16> {
         uint4 kp;
         unsigned w;
     };
-    __device__ static Raw load(const DevProblem &d, int64_t q, bool need_w) {
+    __device__ static Raw load(const DevProblem &d, int64_t q, bool need_w, uint64_t pol) {
         Raw r;
-        r.kp = ld_stream_v4(static_cast<const uint2 *>(d.kp) + q);
-        r.w = need_w ? ld_stream_u32(static_cast<const __half *>(d.w) + q) : 0u;
+        r.kp = ld_stream_v4(static_cast<const uint2 *>(d.kp) + q, pol);
+        r.w = need_w ? ld_stream_u32(static_cast<const __half *>(d.w) + q, pol) : 0u;
         return r;
     }
     __device__ static void get(const Raw &r, int k, float &x1, float &y1, float &x2, float &y2,
@@ -124,10 +159,11 @@ __device__ __forceinline__ void walk_range(const DevProblem &d, int r, int lane,
     int64_t seg_end = d.pair_off[seg + 1];
     float E[9];
     load_E(d.geo, seg, E);
+    const uint64_t pol = evict_first_policy();
     for (int64_t g0 = p_begin; g0 < p_end; g0 += U * GROUP) {
         typename F::Raw raw[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) raw[u] = F::load(d, g0 + u * GROUP + lane * PPL, NEED_W);
+        for (int u = 0; u < U; ++u) raw[u] = F::load(d, g0 + u * GROUP + lane * PPL, NEED_W, pol);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t gb = g0 + u * GROUP;
@@ -154,7 +190,7 @@ __device__ __forceinline__ void walk_range(const DevProblem &d, int r, int lane,
                         }
                     }
                     if (seg_end >= g_end) break;
-                    body.segment_end(seg, r, lane);
+                    body.segment_end(seg, r, lane, false);
                     lo = seg_end;
                     ++seg;
                     seg_end = d.pair_off[seg + 1];
@@ -164,12 +200,24 @@ __device__ __forceinline__ void walk_range(const DevProblem &d, int r, int lane,
             body.group_done(gb, p_end, lane);
         }
     }
-    body.segment_end(seg, r, lane);
+    body.segment_end(seg, r, lane, true);
+}
+
+// (hi, lo) += (bhi, blo) with the rounding error of the high parts kept (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float bhi, float blo) {
+    const float s = hi + bhi;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (bhi - bb);
+    const float l = lo + blo + err;
+    hi = s + l;
+    lo = l - (hi - s);
 }
 
 // ---- loss + adjoint -----------------------------------------------------------------------------
 // acc[0..8] = sum s * o2 o1^T (row-major), acc[9] = sum of loss terms, with s = w*eps (IRLS,
-// the factor 2/Z is applied in combine) or sign(eps) (L1).
+// the factor 2/Z is applied later) or sign(eps) (L1). Each finished (image pair, warp range)
+// intersection is reduced by a warp butterfly into its own slot n + r; no atomics, no fences,
+// a fixed summation order.
 template <int MODE>
 struct LossBody {
     const DevProblem &d;
@@ -199,7 +247,7 @@ struct LossBody {
         acc[7] = fmaf(s, y1, acc[7]);
         acc[8] += s;
     }
-    __device__ __forceinline__ void segment_end(int seg, int r, int lane) {
+    __device__ __forceinline__ void segment_end(int seg, int r, int lane, bool) {
 #pragma unroll
         for (int i = 0; i < 10; ++i) {
             float v = acc[i];
@@ -220,7 +268,9 @@ struct LossBody {
 };
 
 template <int STORE, int MODE>
-__global__ void __launch_bounds__(CTA_WARPS * 32) k_stream_loss(DevProblem d) {
+__global__ void __launch_bounds__(CTA_WARPS * 32, 4) k_stream_loss(DevProblem d) {
+    pdl_wait();     // pair geometry of this pass
+    pdl_trigger();  // the per-camera step may be scheduled once the last wave has started
     const int r = blockIdx.x * CTA_WARPS + (threadIdx.x >> 5);
     if (r >= d.n_ranges) return;
     LossBody<MODE> body(d);
@@ -245,7 +295,7 @@ struct WeightBody {
         out[k] = keep ? 1.0f / fmaxf(a, delta) : 0.f;
         kept += keep ? 1u : 0u;
     }
-    __device__ __forceinline__ void segment_end(int, int, int) {}
+    __device__ __forceinline__ void segment_end(int, int, int, bool) {}
     __device__ __forceinline__ void group_done(int64_t gb, int64_t p_end, int lane) {
         const int64_t q = gb + lane * Fmt<STORE>::PPL;
         if (STORE == FM_STORE_FP32) {
@@ -285,7 +335,7 @@ struct ResidualBody {
     __device__ __forceinline__ void point(int k, float e, float, float, float, float, float) {
         out[k] = e;
     }
-    __device__ __forceinline__ void segment_end(int, int, int) {}
+    __device__ __forceinline__ void segment_end(int, int, int, bool) {}
     __device__ __forceinline__ void group_done(int64_t gb, int64_t p_end, int lane) {
         const int64_t q = gb + lane * Fmt<STORE>::PPL;
 #pragma unroll
@@ -322,22 +372,34 @@ __global__ void k_cam_prep(DevProblem d) {
 }
 
 // ---- per pair: relative pose and folded essential matrix ------------------------------------------
-__global__ void k_pair_setup(DevProblem d) {
+__device__ __forceinline__ void load_camrec(const float *rec, float *R, float *hi, float *lo) {
+    const float4 *v = reinterpret_cast<const float4 *>(rec);
+    const float4 a = v[0], b = v[1], c = v[2], e = v[3];
+    R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w;
+    R[4] = b.x; R[5] = b.y; R[6] = b.z; R[7] = b.w;
+    R[8] = c.x;
+    hi[0] = c.y; hi[1] = c.z; hi[2] = c.w;
+    lo[0] = e.x; lo[1] = e.y; lo[2] = e.z;
+}
+
+__device__ __forceinline__ void finish_step(const DevProblem &d, int n_blocks, int count_step);
+
+// prev_blocks > 0: this pass follows an optimiser step whose camera-step kernel had that many
+// blocks; block 0 (with 256 threads) finishes that step's loss total and step count.
+__global__ void __launch_bounds__(256) k_pair_setup(DevProblem d, int prev_blocks) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = n < d.n_pairs ? d.cam_i[n] : 0, j = n < d.n_pairs ? d.cam_j[n] : 0;
+    pdl_wait();     // camera records of the previous step
+    pdl_trigger();
+    if (prev_blocks > 0 && blockIdx.x == 0) finish_step(d, prev_blocks, 1);
     if (n >= d.n_pairs) return;
-    const int i = d.cam_i[n], j = d.cam_j[n];
-    const float *ci = d.cam + (size_t)i * CAMREC;
-    const float *cj = d.cam + (size_t)j * CAMREC;
-    float Ri[9], Rj[9], dc[3];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        Ri[k] = ci[k];
-        Rj[k] = cj[k];
-    }
+    float Ri[9], Rj[9], hi_i[3], lo_i[3], hi_j[3], lo_j[3], dc[3];
+    load_camrec(d.cam + (size_t)i * CAMREC, Ri, hi_i, lo_i);
+    load_camrec(d.cam + (size_t)j * CAMREC, Rj, hi_j, lo_j);
     // c_i - c_j from the two-float representation: the high parts of nearby centres
     // subtract exactly, so the baseline keeps FP32 relative accuracy far from the origin
 #pragma unroll
-    for (int q = 0; q < 3; ++q) dc[q] = (ci[9 + q] - cj[9 + q]) + (ci[12 + q] - cj[12 + q]);
+    for (int q = 0; q < 3; ++q) dc[q] = (hi_i[q] - hi_j[q]) + (lo_i[q] - lo_j[q]);
     float Rn[9], tn[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -351,7 +413,7 @@ __global__ void k_pair_setup(DevProblem d) {
     // and so E_n, is undefined
     float cmax = 1.f;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) cmax = fmaxf(cmax, fmaxf(fabsf(ci[9 + q]), fabsf(cj[9 + q])));
+    for (int q = 0; q < 3; ++q) cmax = fmaxf(cmax, fmaxf(fabsf(hi_i[q]), fabsf(hi_j[q])));
     const float floor2 = 1e-20f * cmax * cmax;
     float inv = 0.f;
     if (nt2 > floor2 && isfinite(nt2)) {
@@ -370,28 +432,33 @@ __global__ void k_pair_setup(DevProblem d) {
     }
     // E' = T_j^T E T_i with T = [[1,0,cx],[0,1,cy],[0,0,1]] (keypoints stored as offsets o = x - c)
     const float2 cen_i = d.cen[i], cen_j = d.cen[j];
-    float M[9];
+    float g[GEO];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        M[3 * a] = E[3 * a];
-        M[3 * a + 1] = E[3 * a + 1];
-        M[3 * a + 2] = E[3 * a] * cen_i.x + E[3 * a + 1] * cen_i.y + E[3 * a + 2];
+    for (int a = 0; a < 2; ++a) {
+        g[3 * a] = E[3 * a];
+        g[3 * a + 1] = E[3 * a + 1];
+        g[3 * a + 2] = E[3 * a] * cen_i.x + E[3 * a + 1] * cen_i.y + E[3 * a + 2];
     }
-    float *g = d.geo + (size_t)n * GEO;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        g[b] = M[b];
-        g[3 + b] = M[3 + b];
-        g[6 + b] = cen_j.x * M[b] + cen_j.y * M[3 + b] + M[6 + b];
-    }
+    const float m20 = E[6], m21 = E[7], m22 = E[6] * cen_i.x + E[7] * cen_i.y + E[8];
+    g[6] = cen_j.x * g[0] + cen_j.y * g[3] + m20;
+    g[7] = cen_j.x * g[1] + cen_j.y * g[4] + m21;
+    g[8] = cen_j.x * g[2] + cen_j.y * g[5] + m22;
 #pragma unroll
     for (int k = 0; k < 9; ++k) g[9 + k] = Rn[k];
     g[18] = tn[0];
     g[19] = tn[1];
     g[20] = tn[2];
     g[21] = inv;
-    g[22] = 0.f;
-    g[23] = 0.f;
+    g[22] = cen_i.x;
+    g[23] = cen_i.y;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[24 + k] = Rj[k];
+    g[33] = cen_j.x;
+    g[34] = cen_j.y;
+    g[35] = 0.f;
+    float4 *out = reinterpret_cast<float4 *>(d.geo + (size_t)n * GEO);
+#pragma unroll
+    for (int k = 0; k < GEO / 4; ++k) out[k] = make_float4(g[4 * k], g[4 * k + 1], g[4 * k + 2], g[4 * k + 3]);
 }
 
 // ---- per pair: combine partials and chain rule ----------------------------------------------------
@@ -529,18 +596,22 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather(DevProblem d, int cou
 }
 
 // ---- per camera: Adam + exponential map (FP64) -----------------------------------------------------
+// Exp(phi) by Rodrigues' formula, R = I + a K + b K^2 with K = [phi]_x. For |phi| < 0.1
+// (every Adam step: |phi| <= lr) a = sin(t)/t and b = (1 - cos(t))/t^2 come from their Taylor
+// series in t^2 through the t^8 terms (truncation < 3e-18, below half an FP64 ulp of 1),
+// which avoids FP64 sin/cos/sqrt/division on GB300's narrow FP64 pipe.
 __device__ void expmap64(const double *phi, double *R) {
     const double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
-    const double th = sqrt(th2);
     double a, b;
-    if (th < 1e-8) {
-        a = 1.0 - th2 / 6.0;
-        b = 0.5 - th2 / 24.0;
+    if (th2 < 0.01) {
+        a = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0))));
+        b = 0.5 * (1.0 - th2 * (1.0 / 12.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0) * (1.0 - th2 * (1.0 / 90.0)))));
     } else {
-        double s, c;
-        sincos(th, &s, &c);
-        a = s / th;
-        b = (1.0 - c) / th2;
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        a = sn / th;
+        b = (1.0 - cs) / th2;
     }
     const double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
 #pragma unroll
@@ -552,75 +623,340 @@ __device__ void expmap64(const double *phi, double *R) {
         }
 }
 
+// 1/sqrt(x) in FP64: an FP32 seed refined by two Newton steps (the relative error squares
+// each step: ~2e-7 -> ~1e-13 -> below FP64 rounding)
+__device__ __forceinline__ double rsqrt64(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y;
+}
+
 // Gram-Schmidt on the rows: r0 normalised, r1 orthogonalised and normalised, r2 = r0 x r1
 __device__ void orthonormalize_rows(double *R) {
-    const double n0 = 1.0 / sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+    const double n0 = rsqrt64(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
     for (int q = 0; q < 3; ++q) R[q] *= n0;
     const double dp = R[0] * R[3] + R[1] * R[4] + R[2] * R[5];
     for (int q = 0; q < 3; ++q) R[3 + q] -= dp * R[q];
-    const double n1 = 1.0 / sqrt(R[3] * R[3] + R[4] * R[4] + R[5] * R[5]);
+    const double n1 = rsqrt64(R[3] * R[3] + R[4] * R[4] + R[5] * R[5]);
     for (int q = 0; q < 3; ++q) R[3 + q] *= n1;
     R[6] = R[1] * R[5] - R[2] * R[4];
     R[7] = R[2] * R[3] - R[0] * R[5];
     R[8] = R[0] * R[4] - R[1] * R[3];
 }
 
-__global__ void k_adam(DevProblem d) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= d.n_cams) return;
-    const double lr_r = d.hyper[0], lr_c = d.hyper[1], b1 = d.hyper[2], b2 = d.hyper[3],
-                 eps = d.hyper[4];
-    const double t = (double)*d.step;
-    const double bc1 = 1.0 - pow(b1, t), bc2 = 1.0 - pow(b2, t);
-    double delta[6];
+// Chain rule of one image pair (or one range partial of it) to one of its cameras.
+// gr = the pair's geometry record, sum[0..8] = sum s * o2 o1^T over the point pairs,
+// sum[9] = their loss terms. Writes the camera's 6 gradient components and (for the first
+// camera only) the loss.
+__device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const float *sum,
+                                                float gscale, float lscale, float *contrib) {
+    float Gp[9];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const size_t o = (size_t)k * 6 + q;
-        const double g = d.grad[o];
-        const double m = b1 * d.m[o] + (1.0 - b1) * g;
-        const double v = b2 * d.v[o] + (1.0 - b2) * g * g;
-        d.m[o] = m;
-        d.v[o] = v;
-        delta[q] = -(q < 3 ? lr_r : lr_c) * (m / bc1) / (sqrt(v / bc2) + eps);
+    for (int q = 0; q < 9; ++q) Gp[q] = sum[q] * gscale;
+    const float2 cen_i = make_float2(gr[22], gr[23]), cen_j = make_float2(gr[33], gr[34]);
+    float M[9], G[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        M[3 * a] = Gp[3 * a] + Gp[3 * a + 2] * cen_i.x;
+        M[3 * a + 1] = Gp[3 * a + 1] + Gp[3 * a + 2] * cen_i.y;
+        M[3 * a + 2] = Gp[3 * a + 2];
     }
-    double Ex[9], Rk[9], Rn[9];
-    expmap64(delta, Ex);
-    double *R = d.R + (size_t)k * 9;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) Rk[q] = R[q];
+    for (int b = 0; b < 3; ++b) {
+        G[b] = M[b] + cen_j.x * M[6 + b];
+        G[3 + b] = M[3 + b] + cen_j.y * M[6 + b];
+        G[6 + b] = M[6 + b];
+    }
+    const float *Rn = gr + 9;
+    const float tn[3] = {gr[18], gr[19], gr[20]};
+    const float inv = gr[21];
+    const float *Rj = gr + 24;
+    const float th[3] = {tn[0] * inv, tn[1] * inv, tn[2] * inv};
+    float A[9];
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+    for (int b = 0; b < 3; ++b) {
+        A[b] = -(-th[2] * G[3 + b] + th[1] * G[6 + b]);
+        A[3 + b] = -(th[2] * G[b] - th[0] * G[6 + b]);
+        A[6 + b] = -(-th[1] * G[b] + th[0] * G[3 + b]);
+    }
+    float GRt[9];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            Rn[3 * r + c] = Ex[3 * r] * Rk[c] + Ex[3 * r + 1] * Rk[3 + c] + Ex[3 * r + 2] * Rk[6 + c];
-    orthonormalize_rows(Rn);
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int q = 0; q < 9; ++q) R[q] = Rn[q];
-    double *c = d.c + (size_t)k * 3;
+        for (int b = 0; b < 3; ++b)
+            GRt[3 * a + b] = G[3 * a] * Rn[3 * b] + G[3 * a + 1] * Rn[3 * b + 1] + G[3 * a + 2] * Rn[3 * b + 2];
+    float gth[3], gt[3], gc[3], gp[3];
+    vee(GRt, gth);
+    const float dp = th[0] * gth[0] + th[1] * gth[1] + th[2] * gth[2];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) c[q] += delta[3 + q];
-    write_camrec(d.cam + (size_t)k * CAMREC, R, c);
+    for (int q = 0; q < 3; ++q) gt[q] = (gth[q] - dp * th[q]) * inv;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) gc[q] = Rj[q] * gt[0] + Rj[3 + q] * gt[1] + Rj[6 + q] * gt[2];
+    if (role == 0) {
+        float RtA[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) RtA[3 * a + b] = Rn[a] * A[b] + Rn[3 + a] * A[3 + b] + Rn[6 + a] * A[6 + b];
+        vee(RtA, gp);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            contrib[q] = -gp[q];
+            contrib[3 + q] = gc[q];
+        }
+        contrib[6] = sum[9] * lscale;
+    } else {
+        float ARt[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) ARt[3 * a + b] = A[3 * a] * Rn[3 * b] + A[3 * a + 1] * Rn[3 * b + 1] + A[3 * a + 2] * Rn[3 * b + 2];
+        vee(ARt, gp);
+        contrib[0] = gp[0] + (tn[1] * gt[2] - tn[2] * gt[1]);
+        contrib[1] = gp[1] + (tn[2] * gt[0] - tn[0] * gt[2]);
+        contrib[2] = gp[2] + (tn[0] * gt[1] - tn[1] * gt[0]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) contrib[3 + q] = -gc[q];
+        contrib[6] = 0.f;
+    }
+}
+
+// Fused per-camera step, 8 cameras per 256-thread block (all blocks resident at once).
+// Before waiting for the streaming pass (griddepcontrol.wait) the block fetches everything that
+// is at least two kernels old: its cameras' Adam moments, poses and the step count, and for
+// each camera the (pair, role) entries, their range-partial counts and the pairs' geometry
+// records (into shared memory). After the wait only the partial sums remain to be read.
+// Phase 1: warp w owns camera k = 8*block + w. The chain rule is linear in a pair's sums, so it
+// is applied to every (pair, warp-range partial) item separately; the items are spread evenly
+// over the lanes (a pair that spans many ranges does not hold up one lane). The warp reduces
+// the 6 gradient components and the loss with a compensated (TwoSum) FP32 butterfly, so each
+// sum is carried as an unevaluated hi + lo pair.
+// Phase 2: warp 0, one camera per lane: the final per-camera gradient hi + lo in FP64, the
+// Adam update (FP32 moments), R <- Exp(phi) R and Gram-Schmidt re-orthonormalisation in FP64,
+// the centre update in FP64 and the new camera record. Keeping the FP64 work lane-parallel
+// matters on GB300, whose FP64 pipe charges a whole warp instruction per operation.
+// Geometry comes from the pair records of pair_setup, never from another camera's record,
+// which another block may be updating. The loss of a pair is counted by its first camera
+// only; each block writes the FP64 sum of its cameras' losses to cam_loss[block], and the
+// next kernel (pair setup or the finalize kernel) adds them up and advances the step count.
+constexpr int STEP_CAMS = 8;
+
+__global__ void __launch_bounds__(STEP_CAMS * 32, 4)
+k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
+    __shared__ float s_hi[7][STEP_CAMS], s_lo[7][STEP_CAMS];
+    __shared__ int4 s_item[STEP_CAMS][32];
+    __shared__ __align__(16) float s_geo[STEP_CAMS][32][GEO];
+    __shared__ float s_mv[STEP_CAMS][12];     // Adam m (6) and v (6) of the block's cameras
+    __shared__ double s_Rc[STEP_CAMS][12];    // R (9) and c (3) of the block's cameras
+    __shared__ double s_hyper[5];
+    __shared__ double s_loss[STEP_CAMS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * STEP_CAMS + warp;
+    const long long t_step = *d.step + 1;
+    {
+        const int cam0 = blockIdx.x * STEP_CAMS;
+        for (int i = threadIdx.x; i < STEP_CAMS * 12; i += STEP_CAMS * 32) {
+            const int cc = i / 12, q = i % 12;
+            if (cam0 + cc < d.n_cams) {
+                s_mv[cc][q] = q < 6 ? d.m[(size_t)(cam0 + cc) * 6 + q] : d.v[(size_t)(cam0 + cc) * 6 + q - 6];
+                s_Rc[cc][q] = q < 9 ? d.R[(size_t)(cam0 + cc) * 9 + q] : d.c[(size_t)(cam0 + cc) * 3 + q - 9];
+            }
+        }
+        if (threadIdx.x < 5) s_hyper[threadIdx.x] = d.hyper[threadIdx.x];
+    }
+    const int e_begin = k < d.n_cams ? d.cam_off[k] : 0;
+    const int e_end = k < d.n_cams ? d.cam_off[k + 1] : 0;
+    // this camera's entries, 32 at a time: pair, role, first range and number of ranges; the
+    // pair's geometry record goes to shared memory
+    auto load_chunk = [&](int base) -> int {
+        const int e = base + lane;
+        int n = 0, role = 0, r0 = 0, cnt = 0;
+        if (e < e_end) {
+            const int ent = d.cam_ent[e];
+            n = ent >> 1;
+            role = ent & 1;
+            r0 = d.pair_off[n] / WR;
+            cnt = (d.pair_off[n + 1] - 1) / WR - r0 + 1;
+            const float4 *gv = reinterpret_cast<const float4 *>(d.geo + (size_t)n * GEO);
+            float4 *dst = reinterpret_cast<float4 *>(s_geo[warp][lane]);
+#pragma unroll
+            for (int q = 2; q < GEO / 4; ++q) dst[q] = gv[q];
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        s_item[warp][lane] = make_int4(incl - cnt, n, role, r0);
+        __syncwarp();
+        return __shfl_sync(0xffffffffu, incl, 31);
+    };
+    int total = load_chunk(e_begin);
+    pdl_wait();     // partial sums of the streaming pass
+    pdl_trigger();
+    if (k < d.n_cams) {
+        float hi[7], lo[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) hi[q] = lo[q] = 0.f;
+        for (int base = e_begin; base < e_end; base += 32) {
+            if (base != e_begin) {
+                __syncwarp();
+                total = load_chunk(base);
+            }
+            for (int t = lane; t < total; t += 32) {
+                int lo_i = 0, hi_i = 31;
+                while (lo_i < hi_i) {
+                    const int mid = (lo_i + hi_i + 1) >> 1;
+                    if (s_item[warp][mid].x <= t) lo_i = mid;
+                    else hi_i = mid - 1;
+                }
+                const int4 it = s_item[warp][lo_i];
+                const int slot = it.y + it.w + (t - it.x);
+                const float4 *sl = reinterpret_cast<const float4 *>(d.slots + (size_t)slot * SLOT);
+                const float4 sa = sl[0], sb = sl[1], sc = sl[2];
+                const float sum[10] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w, sc.x, sc.y};
+                float contrib[7];
+                pair_chain_rule(s_geo[warp][lo_i], it.z, sum, gscale, lscale, contrib);
+#pragma unroll
+                for (int q = 0; q < 7; ++q) two_sum_acc(hi[q], lo[q], contrib[q], 0.f);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float bh = __shfl_xor_sync(0xffffffffu, hi[q], o);
+                const float bl = __shfl_xor_sync(0xffffffffu, lo[q], o);
+                two_sum_acc(hi[q], lo[q], bh, bl);
+            }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                s_hi[q][warp] = hi[q];
+                s_lo[q][warp] = lo[q];
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0 && lane < STEP_CAMS) {
+        const int kc = blockIdx.x * STEP_CAMS + lane;
+        double bl = 0.0;
+        if (kc < d.n_cams) {
+            double g[6];
+            bool ok = isfinite(s_hi[6][lane]);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                g[q] = (double)s_hi[q][lane] + (double)s_lo[q][lane];
+                ok = ok && isfinite(g[q]);
+            }
+            if (!ok) atomicOr(d.err, ERR_NONFINITE);
+            bl = (double)s_hi[6][lane] + (double)s_lo[6][lane];
+            if (!apply) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) d.grad[(size_t)kc * 6 + q] = g[q];
+            } else {
+                const float b1 = (float)s_hyper[2], b2 = (float)s_hyper[3], eps = (float)s_hyper[4];
+                const float lr_r = (float)s_hyper[0], lr_c = (float)s_hyper[1];
+                const float bc1 = 1.f - powf(b1, (float)t_step), bc2 = 1.f - powf(b2, (float)t_step);
+                double dl[6];
+                float mo[6], vo[6];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const float gq = (float)g[q];
+                    mo[q] = b1 * s_mv[lane][q] + (1.f - b1) * gq;
+                    vo[q] = b2 * s_mv[lane][6 + q] + (1.f - b2) * gq * gq;
+                    dl[q] = (double)(-(q < 3 ? lr_r : lr_c) * (mo[q] / bc1) / (sqrtf(vo[q] / bc2) + eps));
+                }
+                double Ex[9], Rn[9], cn[3];
+                expmap64(dl, Ex);
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        Rn[3 * r + c] = Ex[3 * r] * s_Rc[lane][c] + Ex[3 * r + 1] * s_Rc[lane][3 + c] +
+                                        Ex[3 * r + 2] * s_Rc[lane][6 + c];
+                orthonormalize_rows(Rn);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) cn[q] = s_Rc[lane][9 + q] + dl[3 + q];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const size_t o = (size_t)kc * 6 + q;
+                    d.m[o] = mo[q];
+                    d.v[o] = vo[q];
+                    d.grad[o] = g[q];
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) d.R[(size_t)kc * 9 + q] = Rn[q];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) d.c[(size_t)kc * 3 + q] = cn[q];
+                write_camrec(d.cam + (size_t)kc * CAMREC, Rn, cn);
+            }
+        }
+        s_loss[lane] = bl;
+        __syncwarp(0xffu);
+        if (lane == 0) {
+            double b = 0.0;
+#pragma unroll
+            for (int q = 0; q < STEP_CAMS; ++q) b += s_loss[q];
+            d.cam_loss[blockIdx.x] = b;
+        }
+    }
+}
+
+// Loss total of a camera-step launch (FP64, fixed order over its blocks) and, after an
+// optimiser step, the step count. One block.
+constexpr int FIN_THREADS = 256;
+
+__device__ __forceinline__ void finish_step(const DevProblem &d, int n_blocks, int count_step) {
+    __shared__ double red[FIN_THREADS];
+    double s = 0.0;
+    for (int q = threadIdx.x; q < n_blocks; q += FIN_THREADS) s += d.cam_loss[q];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = FIN_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *d.loss_out = red[0];
+        if (count_step) *d.step += 1;
+    }
+}
+
+__global__ void __launch_bounds__(FIN_THREADS) k_finalize(DevProblem d, int n_blocks, int count_step) {
+    pdl_wait();
+    pdl_trigger();
+    finish_step(d, n_blocks, count_step);
 }
 
 // ---- launchers -------------------------------------------------------------------------------------
 static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
+int camera_step_blocks(const DevProblem &d) { return blocks_for(d.n_cams, STEP_CAMS); }
+
 void launch_cam_prep(const DevProblem &d, cudaStream_t s) {
     k_cam_prep<<<blocks_for(d.n_cams, 128), 128, 0, s>>>(d);
 }
 
-void launch_pair_setup(const DevProblem &d, cudaStream_t s) {
-    k_pair_setup<<<blocks_for(d.n_pairs, 128), 128, 0, s>>>(d);
+void launch_pair_setup(const DevProblem &d, cudaStream_t s, bool pdl, bool after_step) {
+    launch_k(k_pair_setup, dim3(blocks_for(d.n_pairs, 256)), dim3(256), s, pdl, d,
+             after_step ? camera_step_blocks(d) : 0);
 }
 
-void launch_stream_loss(const DevProblem &d, cudaStream_t s) {
-    const int grid = blocks_for(d.n_ranges, CTA_WARPS);
+void launch_finalize(const DevProblem &d, bool count_step, cudaStream_t s, bool pdl) {
+    launch_k(k_finalize, dim3(1), dim3(FIN_THREADS), s, pdl, d, camera_step_blocks(d), count_step ? 1 : 0);
+}
+
+void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl) {
+    const dim3 grid(blocks_for(d.n_ranges, CTA_WARPS)), block(CTA_WARPS * 32);
     if (d.storage == FM_STORE_FP32) {
-        if (d.loss == FM_LOSS_IRLS) k_stream_loss<FM_STORE_FP32, MODE_LOSS_IRLS><<<grid, CTA_WARPS * 32, 0, s>>>(d);
-        else k_stream_loss<FM_STORE_FP32, MODE_LOSS_L1><<<grid, CTA_WARPS * 32, 0, s>>>(d);
+        if (d.loss == FM_LOSS_IRLS) launch_k(k_stream_loss<FM_STORE_FP32, MODE_LOSS_IRLS>, grid, block, s, pdl, d);
+        else launch_k(k_stream_loss<FM_STORE_FP32, MODE_LOSS_L1>, grid, block, s, pdl, d);
     } else {
-        if (d.loss == FM_LOSS_IRLS) k_stream_loss<FM_STORE_FP16, MODE_LOSS_IRLS><<<grid, CTA_WARPS * 32, 0, s>>>(d);
-        else k_stream_loss<FM_STORE_FP16, MODE_LOSS_L1><<<grid, CTA_WARPS * 32, 0, s>>>(d);
+        if (d.loss == FM_LOSS_IRLS) launch_k(k_stream_loss<FM_STORE_FP16, MODE_LOSS_IRLS>, grid, block, s, pdl, d);
+        else launch_k(k_stream_loss<FM_STORE_FP16, MODE_LOSS_L1>, grid, block, s, pdl, d);
     }
 }
 
@@ -641,8 +977,22 @@ void launch_gather(const DevProblem &d, bool count_step, cudaStream_t s) {
     k_gather<<<blocks_for(d.n_cams, GATHER_THREADS) + 1, GATHER_THREADS, 0, s>>>(d, count_step ? 1 : 0);
 }
 
-void launch_adam(const DevProblem &d, cudaStream_t s) {
-    k_adam<<<blocks_for(d.n_cams, 64), 64, 0, s>>>(d);
+static void loss_scales(const DevProblem &d, float &gscale, float &lscale) {
+    const double Z = (double)d.n_pp;
+    if (d.loss == FM_LOSS_IRLS) {  // stored weights are w * s
+        gscale = (float)(2.0 / (Z * d.w_scale));
+        lscale = (float)(1.0 / (Z * d.w_scale));
+    } else {
+        gscale = (float)(1.0 / Z);
+        lscale = (float)(1.0 / Z);
+    }
+}
+
+void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl) {
+    float gscale, lscale;
+    loss_scales(d, gscale, lscale);
+    launch_k(k_camera_step, dim3(blocks_for(d.n_cams, STEP_CAMS)), dim3(STEP_CAMS * 32), s, pdl, d,
+             gscale, lscale, apply ? 1 : 0);
 }
 
 void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s) {

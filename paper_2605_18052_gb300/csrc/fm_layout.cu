@@ -220,46 +220,65 @@ void launch_range_pairs(const int *pair_off, int n_pairs, int n_ranges, int *ran
 // ---- per-image centroids (FP16 storage) ---------------------------------------------------------------
 // c_k = mean of every keypoint of image k over all its pairs, summed exactly as trunc(x * 2^32)
 // in int64 (order-independent), then (double)sum / count * 2^-32 rounded to FP32.
-__global__ void k_centroid_sums(const int *keys, const int *perm, const float2 *x1,
-                                const float2 *x2, int64_t n, const int *cam_i, const int *cam_j,
-                                unsigned long long *sums) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = p < n;
-    const int lane = threadIdx.x & 31;
-    int key = 0;
-    long long f[4] = {0, 0, 0, 0};
-    if (valid) {
-        key = keys[p];
-        const int64_t src = perm ? perm[p] : p;
-        const float2 a = x1[src], b = x2[src];
-        const float sc = 4294967296.0f;  // 2^FIXED_SHIFT
-        f[0] = __float2ll_rz(a.x * sc);
-        f[1] = __float2ll_rz(a.y * sc);
-        f[2] = __float2ll_rz(b.x * sc);
-        f[3] = __float2ll_rz(b.y * sc);
-    }
-    const unsigned act = __ballot_sync(0xffffffffu, valid);
-    const int key0 = __shfl_sync(0xffffffffu, key, 0);
-    const bool uniform = act == 0xffffffffu && __all_sync(0xffffffffu, key == key0);
-    if (uniform) {
+// Warp r walks the sorted point pairs of warp range r (as the streaming kernels do) and keeps
+// the four fixed-point sums of the current image pair in registers; when the pair ends the
+// warp reduces them and lane 0 adds them to the pair's two cameras (one atomic set per
+// (range, pair) intersection, integer adds, so the result does not depend on their order).
+__device__ __forceinline__ void centroid_flush(const DevProblem &d, int seg, int lane,
+                                               long long *f, unsigned long long *sums) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
-        if (lane == 0) {
-            const int i = cam_i[key], j = cam_j[key];
-            atomicAdd(&sums[2 * i], (unsigned long long)f[0]);
-            atomicAdd(&sums[2 * i + 1], (unsigned long long)f[1]);
-            atomicAdd(&sums[2 * j], (unsigned long long)f[2]);
-            atomicAdd(&sums[2 * j + 1], (unsigned long long)f[3]);
-        }
-    } else if (valid) {
-        const int i = cam_i[key], j = cam_j[key];
+        for (int o = 16; o > 0; o >>= 1) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
+    if (lane == 0) {
+        const int i = d.cam_i[seg], j = d.cam_j[seg];
         atomicAdd(&sums[2 * i], (unsigned long long)f[0]);
         atomicAdd(&sums[2 * i + 1], (unsigned long long)f[1]);
         atomicAdd(&sums[2 * j], (unsigned long long)f[2]);
         atomicAdd(&sums[2 * j + 1], (unsigned long long)f[3]);
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f[q] = 0;
+}
+
+__global__ void k_centroid_sums(DevProblem d, const float2 *x1, const float2 *x2,
+                                unsigned long long *sums) {
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= d.n_ranges) return;
+    const int64_t p_begin = (int64_t)r * WR;
+    const int64_t p_end = min(p_begin + (int64_t)WR, d.n_pp);
+    int seg = d.range_pair[r];
+    int64_t seg_end = d.pair_off[seg + 1];
+    long long f[4] = {0, 0, 0, 0};
+    const float sc = 4294967296.0f;  // 2^FIXED_SHIFT
+    for (int64_t gb = p_begin; gb < p_end; gb += 32) {
+        const int64_t q = gb + lane;
+        long long v[4] = {0, 0, 0, 0};
+        if (q < p_end) {
+            const int64_t src = d.perm ? d.perm[q] : q;
+            const float2 a = x1[src], b = x2[src];
+            v[0] = __float2ll_rz(a.x * sc);
+            v[1] = __float2ll_rz(a.y * sc);
+            v[2] = __float2ll_rz(b.x * sc);
+            v[3] = __float2ll_rz(b.y * sc);
+        }
+        int64_t lo = gb;
+        const int64_t g_end = min(gb + 32, p_end);
+        while (true) {
+            const int64_t hi = min(seg_end, p_end);
+            if (q >= lo && q < hi) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[k] += v[k];
+            }
+            if (seg_end >= g_end) break;
+            centroid_flush(d, seg, lane, f, sums);
+            lo = seg_end;
+            ++seg;
+            seg_end = d.pair_off[seg + 1];
+        }
+    }
+    centroid_flush(d, seg, lane, f, sums);
 }
 
 __global__ void k_centroid_final(const unsigned long long *sums, const int *cam_off,
@@ -283,9 +302,9 @@ __global__ void k_centroid_final(const unsigned long long *sums, const int *cam_
 
 void launch_centroids(const DevProblem &d, const int *sorted_keys, const float2 *x1,
                       const float2 *x2, unsigned long long *sums, cudaStream_t s) {
+    (void)sorted_keys;  // the walk uses pair_off and range_pair instead
     cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * 2 * d.n_cams, s);
-    k_centroid_sums<<<blocks_for(d.n_pp, 256), 256, 0, s>>>(sorted_keys, d.perm, x1, x2, d.n_pp,
-                                                           d.cam_i, d.cam_j, sums);
+    k_centroid_sums<<<blocks_for(d.n_ranges, 8), 256, 0, s>>>(d, x1, x2, sums);
     k_centroid_final<<<blocks_for(d.n_cams, 128), 128, 0, s>>>(sums, d.cam_off, d.cam_ent,
                                                               d.pair_off, d.n_cams, d.cen);
 }
