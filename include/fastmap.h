@@ -143,6 +143,9 @@ FM_API fm_status fm_set_poses(fm_problem *p, const double *R, const double *t);
  */
 FM_API fm_status fm_get_params(fm_problem *p, double *R, double *c);
 FM_API fm_status fm_set_params(fm_problem *p, const double *R, const double *c);
+/* fm_set_params from device memory (d_R n_cams x 9, d_c n_cams x 3, FP64), asynchronous and
+ * ordered on the caller's stream; R must be a rotation (not checked here). */
+FM_API fm_status fm_set_params_device(fm_problem *p, const double *d_R, const double *d_c);
 
 /*
  * Replace the per-point-pair weights w of the IRLS objective (n_pp FP32, input order; host,

@@ -6,6 +6,7 @@ runs every per-point-pair pass; this package is its Python binding plus host-sid
 from .binding import (FM_LOSS_IRLS, FM_LOSS_L1, FM_STORE_FP16, FM_STORE_FP32, FastMapError,
                       Options, Problem, default_options, load_library)
 from .refine import Schedule, refine
+from .autograd import EpipolarLoss, epipolar_loss
 
 __all__ = ["Problem", "Options", "default_options", "load_library", "FastMapError", "Schedule",
-           "refine", "FM_STORE_FP32", "FM_STORE_FP16", "FM_LOSS_IRLS", "FM_LOSS_L1"]
+           "refine", "EpipolarLoss", "epipolar_loss", "FM_STORE_FP32", "FM_STORE_FP16", "FM_LOSS_IRLS", "FM_LOSS_L1"]

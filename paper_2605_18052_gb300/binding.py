@@ -18,7 +18,7 @@ FM_LOSS_IRLS, FM_LOSS_L1 = 0, 1
 
 EXPORTED = [
     "fm_default_options", "fm_create_problem", "fm_destroy_problem", "fm_problem_info",
-    "fm_get_poses", "fm_set_poses", "fm_get_params", "fm_set_params", "fm_set_weights", "fm_get_weights", "fm_irls_weights",
+    "fm_get_poses", "fm_set_poses", "fm_get_params", "fm_set_params", "fm_set_params_device", "fm_set_weights", "fm_get_weights", "fm_irls_weights",
     "fm_loss_grad", "fm_loss_grad_device", "fm_residuals", "fm_step", "fm_last_loss",
     "fm_set_learning_rate", "fm_reset_optimizer", "fm_get_state", "fm_set_state",
     "fm_synchronize", "fm_enable_kernel_timing", "fm_kernel_time", "fm_loss_grad_noalloc",
@@ -68,6 +68,7 @@ def load_library(path: str = LIB_PATH):
         "fm_set_poses": (I32, [P, P, P]),
         "fm_get_params": (I32, [P, P, P]),
         "fm_set_params": (I32, [P, P, P]),
+        "fm_set_params_device": (I32, [P, P, P]),
         "fm_set_weights": (I32, [P, P, I32]),
         "fm_get_weights": (I32, [P, P]),
         "fm_irls_weights": (I32, [P, D, P]),
@@ -220,6 +221,11 @@ class Problem:
         R = _host(R, np.float64)
         c = _host(c, np.float64)
         _check(load_library().fm_set_params(self._h, _ptr(R), _ptr(c)))
+
+    def set_params_device(self, R, c):
+        """Asynchronous parameter update from contiguous float64 CUDA tensors (N,3,3), (N,3)."""
+        _check(load_library().fm_set_params_device(self._h, ctypes.c_void_p(R.data_ptr()),
+                                                   ctypes.c_void_p(c.data_ptr())))
 
     def set_weights(self, w):
         if _is_cuda(w):

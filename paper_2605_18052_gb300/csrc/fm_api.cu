@@ -507,6 +507,19 @@ FM_API fm_status fm_set_params(fm_problem *p, const double *R, const double *c) 
     return FM_OK;
 }
 
+FM_API fm_status fm_set_params_device(fm_problem *p, const double *d_R, const double *d_c) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!d_R || !d_c) return fail(FM_EINVAL, "d_R and d_c must not be NULL");
+    const int n = p->d.n_cams;
+    FM_CUDA(join_in(p));
+    FM_CUDA(cudaMemcpyAsync(p->d.R, d_R, sizeof(double) * 9 * n, cudaMemcpyDeviceToDevice, p->s));
+    FM_CUDA(cudaMemcpyAsync(p->d.c, d_c, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, p->s));
+    launch_cam_prep(p->d, p->s);
+    FM_CUDA(cudaGetLastError());
+    FM_CUDA(join_out(p));
+    return FM_OK;
+}
+
 FM_API fm_status fm_set_weights(fm_problem *p, const float *w, int32_t on_device) {
     if (fm_status st = check_problem(p)) return st;
     if (!w) return fail(FM_EINVAL, "w must not be NULL");
