@@ -130,8 +130,8 @@ def schedule_for(sc, iters):
     C = -(R.transpose(1, 2) @ t[:, :, None])[:, :, 0]
     base = float((C[sc.cam_i.long()] - C[sc.cam_j.long()]).norm(dim=1).median())
     rounds = max(1, sc.iters // iters)
-    return Schedule(rounds=rounds, iters_per_round=iters, tau0=0.05, tau_min=4 * sc.sigma_px / sc.f,
-                    decay=0.9, lr_rot=1e-2, lr_c=1e-2 * base)
+    return Schedule(rounds=rounds, iters_per_round=iters, tau0=0.5, tau_min=4 * sc.sigma_px / sc.f,
+                    tau_factor=0.8, decay=0.95, lr_rot=1e-2, lr_c=1e-2 * base)
 
 
 def cpu_oracle_rate(sc, seconds: float):

@@ -19,8 +19,8 @@ this module loads it with ctypes and adds the small dense pieces in NumPy:
 
 Where the paper is silent the readings are: E_n uses the unit translation t_n/|t_n|; the
 quadratic-form factor is 1/Z (the printed 2/Z does not match (w^T e)^2 = e^T w w^T e);
-w = 1/max(|eps^|, delta); filtered pairs keep counting in Z; the filter threshold halves
-each round down to a floor; Adam state persists across rounds; the per-camera parameters
+w = 1/max(|eps^|, delta); filtered pairs keep counting in Z; the filter threshold shrinks
+by a constant factor each round down to a floor; Adam state persists across rounds; the per-camera parameters
 are a left rotation increment and the camera centre.
 
 Pinned by the not-gpu tests against: zero residual at the true poses of noise-free scenes,
@@ -188,9 +188,11 @@ def irls_weights(eps_hat, tau: float, delta: float):
     return w, int(kept)
 
 
-def threshold_schedule(r: int, tau0: float, tau_min: float) -> float:
-    """Filtering threshold of round r: starts large and halves each round down to a floor."""
-    return max(tau_min, tau0 * 0.5 ** r)
+def threshold_schedule(r: int, tau0: float, tau_min: float, factor: float = 0.8) -> float:
+    """Filtering threshold of round r: starts large and shrinks by `factor` each round down to
+    a floor ("a relatively large initial threshold ... gradually decrease to a pre-determined
+    minimum")."""
+    return max(tau_min, tau0 * factor ** r)
 
 
 # ---- optimiser ----------------------------------------------------------------------------
@@ -222,7 +224,8 @@ def adam_step(R, c, grad, m, v, step: int, lr_rot: float, lr_c: float,
 
 def refine(prob: Problem, R0, c0, n_rounds: int, iters_per_round: int, tau0: float,
            tau_min: float, delta: float, lr_rot: float, lr_c: float, decay: float = 1.0,
-           beta1=0.9, beta2=0.999, adam_eps=1e-12, weight_fn=None, callback=None):
+           beta1=0.9, beta2=0.999, adam_eps=1e-12, weight_fn=None, callback=None,
+           tau_factor: float = 0.8):
     """IRLS epipolar adjustment: per round, reweight at the current poses (with filtering),
     then `iters_per_round` Adam steps on the weighted objective. Learning rates are
     multiplied by `decay` after every round. `weight_fn(w)` may post-process the weights
@@ -234,7 +237,7 @@ def refine(prob: Problem, R0, c0, n_rounds: int, iters_per_round: int, tau0: flo
     step = 0
     loss = float("nan")
     for r in range(n_rounds):
-        tau = threshold_schedule(r, tau0, tau_min)
+        tau = threshold_schedule(r, tau0, tau_min, tau_factor)
         w, _ = irls_weights(residuals(prob, R, c), tau, delta)
         if weight_fn is not None:
             w = weight_fn(w)

@@ -1,8 +1,8 @@
 """IRLS epipolar adjustment driver (Sec. "Epipolar Adjustment"): host control flow only.
 
 Each round reweights the point pairs at the current poses with a filtering threshold that
-starts large and halves every round down to a floor, then runs a fixed number of Adam
-iterations on the reweighted objective. All per-point-pair work happens inside the library
+starts large and shrinks by a constant factor every round down to a floor, then runs a fixed
+number of Adam iterations on the reweighted objective. All per-point-pair work happens inside the library
 calls (fm_irls_weights, fm_step).
 """
 from __future__ import annotations
@@ -14,14 +14,15 @@ import dataclasses
 class Schedule:
     rounds: int = 8
     iters_per_round: int = 25
-    tau0: float = 0.05        # initial filtering threshold (normalized epipolar error)
+    tau0: float = 0.5         # initial filtering threshold (normalized epipolar error)
     tau_min: float = 0.004    # threshold floor
-    decay: float = 0.9        # learning-rate factor per round
+    tau_factor: float = 0.8   # threshold factor per round
+    decay: float = 0.95       # learning-rate factor per round
     lr_rot: float = 1e-2      # radians
     lr_c: float = 1e-2        # scene units (scale with the typical baseline)
 
     def tau(self, r: int) -> float:
-        return max(self.tau_min, self.tau0 * 0.5 ** r)
+        return max(self.tau_min, self.tau0 * self.tau_factor ** r)
 
 
 def refine(problem, schedule: Schedule, callback=None, first_round: int = 0):

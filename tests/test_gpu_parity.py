@@ -228,13 +228,14 @@ def test_refine_schedule_matches_oracle_accuracy():
     cg = O.centres_from_poses(Rg, sc.t_gt.numpy())
     prob = O.Problem.from_scene(sc)
     base = float(np.median(np.linalg.norm(cg[prob.cam_i] - cg[prob.cam_j], axis=1)))
-    sch = fm.Schedule(rounds=12, iters_per_round=25, tau0=0.05, tau_min=4 * sc.sigma_px / sc.f,
-                      decay=0.9, lr_rot=1e-2, lr_c=1e-2 * base)
+    sch = fm.Schedule(rounds=12, iters_per_round=25, tau0=0.5, tau_min=4 * sc.sigma_px / sc.f,
+                      tau_factor=0.8, decay=0.95, lr_rot=1e-2, lr_c=1e-2 * base)
     with _gpu_problem(sc, R0, t0) as gp:
         fm.refine(gp, sch)
         R_g, t_g = gp.get_poses()
     R_o, c_o, _ = O.refine(prob, R0, O.centres_from_poses(R0, t0), sch.rounds, sch.iters_per_round,
-                           sch.tau0, sch.tau_min, 1e-6, sch.lr_rot, sch.lr_c, sch.decay)
+                           sch.tau0, sch.tau_min, 1e-6, sch.lr_rot, sch.lr_c, sch.decay,
+                           tau_factor=sch.tau_factor)
     e_g = O.rotation_error_deg(R_g, Rg).mean()
     e_o = O.rotation_error_deg(R_o, Rg).mean()
     e0 = O.rotation_error_deg(R0, Rg).mean()

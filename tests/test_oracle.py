@@ -230,8 +230,10 @@ def test_irls_filter_and_floor_closed_form():
 
 
 def test_threshold_schedule():
-    assert [O.threshold_schedule(r, 0.05, 0.004) for r in range(6)] == \
+    assert [O.threshold_schedule(r, 0.05, 0.004, 0.5) for r in range(6)] == \
         [0.05, 0.025, 0.0125, 0.00625, 0.004, 0.004]
+    assert O.threshold_schedule(3, 0.5, 0.008) == pytest.approx(0.5 * 0.8 ** 3)
+    assert O.threshold_schedule(40, 0.5, 0.008) == 0.008
 
 
 # ---- optimiser ----------------------------------------------------------------------------------
@@ -284,7 +286,7 @@ def test_refine_moves_towards_truth_noise_free():
     l0 = O.loss_grad(prob, R0, c0)[0]
     e0 = O.rotation_error_deg(R0, Rg).mean()
     base = np.median(np.linalg.norm(cg[prob.cam_i] - cg[prob.cam_j], axis=1))
-    R, c, _ = O.refine(prob, R0, c0, 12, 25, 1.0, 1.0, 1e-9, 1e-2, 1e-2 * base, 0.9,
+    R, c, _ = O.refine(prob, R0, c0, 12, 25, 1.0, 1.0, 1e-9, 1e-2, 1e-2 * base, 0.95,
                        weight_fn=lambda w: np.ones_like(w))
     assert O.loss_grad(prob, R, c)[0] < 1e-2 * l0
     assert O.rotation_error_deg(R, Rg).mean() < e0 / 3
