@@ -202,6 +202,51 @@ FM_API fm_status fm_reset_optimizer(fm_problem *p);
 FM_API fm_status fm_get_state(fm_problem *p, double *m, double *v, int64_t *step);
 FM_API fm_status fm_set_state(fm_problem *p, const double *m, const double *v, int64_t step);
 
+/* ---- learned inlier weights ------------------------------------------------------------------
+ * The thesis has no learned component. These entry points implement the learned variant of the
+ * reweighting step the benchmark describes: an MLP 8 -> 32 -> 32 -> 1 (ReLU, sigmoid) predicts
+ * the probability p that a point pair is an inlier, and the IRLS weight becomes
+ * w = p / max(|eps^|, delta) (0 where |eps^| > tau_cap). Features of a point pair, from the
+ * residuals eps^ at the current poses (Sec. "Epipolar Adjustment" notation):
+ *   0 log(|e|+1e-6) - log(tau)        1 log(|e|+1e-6) - mean over its image pair of log(|e|+1e-6)
+ *   2 log(|e_prev|+1e-6) - log(|e|+1e-6)   (e_prev: residual at the previous reweighting call)
+ *   3 match score                     4 fraction of its image pair's point pairs with |e| <= tau
+ *   5 log(image-pair size)/10         6 round/10        7 log(|e_prev|+1e-6) - log(tau)
+ * Numerics: features, weights and hidden activations in BF16, FP32 accumulation, FP32 biases.
+ * Parameters: 1377 FP32 values, W1 (8 x 32, row k = input), b1 (32), W2 (32 x 32), b2 (32),
+ * W3 (32), b3 (1).
+ */
+typedef struct fm_mlp fm_mlp;
+
+FM_API int32_t fm_mlp_num_params(void);
+/* Network from host FP32 parameters (copied); the device keeps FP32 masters and BF16 copies. */
+FM_API fm_status fm_mlp_create(const float *params, fm_mlp **out);
+FM_API void fm_mlp_destroy(fm_mlp *net);
+FM_API fm_status fm_mlp_get_params(fm_mlp *net, float *params);
+FM_API fm_status fm_mlp_set_params(fm_mlp *net, const float *params);
+/* One Adam step (beta 0.9/0.999, eps 1e-8) on the mean binary cross-entropy of count samples:
+ * d_features (count x 8 BF16, device), d_labels (count FP32 in {0,1}, device), count <= 65536.
+ * Writes the batch loss before the step to *loss (host; may be NULL, then nothing syncs). */
+FM_API fm_status fm_mlp_train_step(fm_mlp *net, const void *d_features, const float *d_labels,
+                                   int32_t count, float lr, float *loss, void *stream);
+/* Gradient of the mean cross-entropy (host, fm_mlp_num_params() floats) without a step. */
+FM_API fm_status fm_mlp_gradient(fm_mlp *net, const void *d_features, const float *d_labels,
+                                 int32_t count, float *grad, float *loss);
+/* p for count feature rows (device BF16 in, device FP32 out), asynchronous on `stream`. */
+FM_API fm_status fm_mlp_forward(fm_mlp *net, const void *d_features, int32_t count, float *d_p,
+                                void *stream);
+/* Match scores in [0, 1] (n_pp FP32, input order; host, or device when on_device is 1). */
+FM_API fm_status fm_set_scores(fm_problem *p, const float *score, int32_t on_device);
+/* Features of every point pair at the current poses (d_features: n_pp x 8 BF16, device, input
+ * order), then remember the residuals as the history of the next call. Synchronises. */
+FM_API fm_status fm_collect_features(fm_problem *p, double tau, int32_t round, void *d_features);
+/* Learned reweighting (replaces fm_irls_weights): features -> MLP (tensor cores) -> weights;
+ * n_active counts point pairs with |eps^| <= tau_cap. Synchronises. */
+FM_API fm_status fm_learned_weights(fm_problem *p, const fm_mlp *net, double tau, double tau_cap,
+                                    int32_t round, int64_t *n_active);
+/* Forget the residual history (the next call uses the current residuals as history). */
+FM_API fm_status fm_reset_history(fm_problem *p);
+
 /* Wait for all queued work of the problem; returns FM_EDEGENERATE if the device flagged one. */
 FM_API fm_status fm_synchronize(fm_problem *p);
 

@@ -57,6 +57,73 @@ def features(abs_eps, abs_eps_prev, score, pair_id, n_pairs, tau, round_index):
     return f
 
 
+# ---- flat parameter vector (the library's layout) and BF16 emulation -----------------------------
+SHAPES = (("W1", (N_FEAT, HIDDEN)), ("b1", (HIDDEN,)), ("W2", (HIDDEN, HIDDEN)), ("b2", (HIDDEN,)),
+          ("W3", (HIDDEN, 1)), ("b3", (1,)))
+
+
+def flatten(params) -> np.ndarray:
+    return np.concatenate([np.asarray(params[k], np.float64).reshape(-1) for k, _ in SHAPES])
+
+
+def unflatten(vec) -> dict:
+    vec = np.asarray(vec, np.float64)
+    out, o = {}, 0
+    for k, shp in SHAPES:
+        n = int(np.prod(shp))
+        out[k] = vec[o:o + n].reshape(shp).copy()
+        o += n
+    return out
+
+
+def bf16_round(x) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), returned as float64: the FP32 bit pattern
+    with the low 16 bits rounded away."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def quantized(params) -> dict:
+    """Weights rounded to BF16 (biases stay as they are), as the library uses them."""
+    q = {k: np.asarray(v, np.float64).copy() for k, v in params.items()}
+    for k in ("W1", "W2", "W3"):
+        q[k] = bf16_round(q[k])
+    return q
+
+
+def forward_bf16(params, X, keep=False):
+    """The library's numerics: BF16 inputs, weights and hidden activations, exact products."""
+    qp = quantized(params)
+    xb = bf16_round(X)
+    z1 = xb @ qp["W1"] + qp["b1"]
+    h1 = bf16_round(np.maximum(z1, 0.0))
+    z2 = h1 @ qp["W2"] + qp["b2"]
+    h2 = bf16_round(np.maximum(z2, 0.0))
+    z3 = (h2 @ qp["W3"])[:, 0] + qp["b3"][0]
+    p = 1.0 / (1.0 + np.exp(-z3))
+    if keep:
+        return p, (xb, z1, h1, z2, h2, z3, qp)
+    return p
+
+
+def bce_loss_grad_bf16(params, X, y):
+    """Cross-entropy gradient of forward_bf16 with the roundings passed straight through."""
+    p, (xb, z1, h1, z2, h2, z3, qp) = forward_bf16(params, X, keep=True)
+    n = X.shape[0]
+    loss = np.mean(np.maximum(z3, 0) - z3 * y + np.log1p(np.exp(-np.abs(z3))))
+    dz3 = (p - y) / n
+    g = {"W3": h2.T @ dz3[:, None], "b3": np.array([dz3.sum()])}
+    dz2 = dz3[:, None] * qp["W3"][:, 0][None, :] * (z2 > 0)
+    g["W2"] = h1.T @ dz2
+    g["b2"] = dz2.sum(0)
+    dz1 = (dz2 @ qp["W2"].T) * (z1 > 0)
+    g["W1"] = xb.T @ dz1
+    g["b1"] = dz1.sum(0)
+    return loss, g
+
+
 def init_params(seed=0):
     rng = np.random.default_rng(seed)
     return {

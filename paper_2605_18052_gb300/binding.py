@@ -22,7 +22,9 @@ EXPORTED = [
     "fm_loss_grad", "fm_loss_grad_device", "fm_residuals", "fm_step", "fm_last_loss",
     "fm_set_learning_rate", "fm_reset_optimizer", "fm_get_state", "fm_set_state",
     "fm_synchronize", "fm_enable_kernel_timing", "fm_kernel_time", "fm_loss_grad_noalloc",
-    "fm_status_string", "fm_last_error",
+    "fm_status_string", "fm_last_error", "fm_mlp_num_params", "fm_mlp_create", "fm_mlp_destroy",
+    "fm_mlp_get_params", "fm_mlp_set_params", "fm_mlp_train_step", "fm_mlp_gradient", "fm_mlp_forward",
+    "fm_set_scores", "fm_collect_features", "fm_learned_weights", "fm_reset_history",
 ]
 
 
@@ -85,6 +87,18 @@ def load_library(path: str = LIB_PATH):
         "fm_enable_kernel_timing": (I32, [P, I32]),
         "fm_kernel_time": (I32, [P, P, P]),
         "fm_loss_grad_noalloc": (I32, [I32, P, P, I32, P, P, P, I64, P, P, I32, P, P, P]),
+        "fm_mlp_num_params": (I32, []),
+        "fm_mlp_create": (I32, [P, P]),
+        "fm_mlp_destroy": (None, [P]),
+        "fm_mlp_get_params": (I32, [P, P]),
+        "fm_mlp_set_params": (I32, [P, P]),
+        "fm_mlp_train_step": (I32, [P, P, P, I32, ctypes.c_float, P, P]),
+        "fm_mlp_gradient": (I32, [P, P, P, I32, P, P]),
+        "fm_mlp_forward": (I32, [P, P, I32, P, P]),
+        "fm_set_scores": (I32, [P, P, I32]),
+        "fm_collect_features": (I32, [P, D, I32, P]),
+        "fm_learned_weights": (I32, [P, P, D, D, I32, P]),
+        "fm_reset_history": (I32, [P]),
         "fm_status_string": (ctypes.c_char_p, [I32]),
         "fm_last_error": (ctypes.c_char_p, []),
     }
@@ -227,6 +241,29 @@ class Problem:
         _check(load_library().fm_set_params_device(self._h, ctypes.c_void_p(R.data_ptr()),
                                                    ctypes.c_void_p(c.data_ptr())))
 
+    def set_scores(self, score):
+        if _is_cuda(score):
+            import torch
+            score = score.to(torch.float32).contiguous()
+            _check(load_library().fm_set_scores(self._h, ctypes.c_void_p(score.data_ptr()), 1))
+        else:
+            sv = _host(score, np.float32)
+            _check(load_library().fm_set_scores(self._h, _ptr(sv), 0))
+
+    def collect_features(self, tau: float, round_index: int, out):
+        """Features of every point pair (out: CUDA bfloat16 tensor n_pp x 8, input order)."""
+        _check(load_library().fm_collect_features(self._h, float(tau), int(round_index),
+                                                  ctypes.c_void_p(out.data_ptr())))
+
+    def learned_weights(self, net: "Mlp", tau: float, tau_cap: float, round_index: int) -> int:
+        n = ctypes.c_int64()
+        _check(load_library().fm_learned_weights(self._h, net._h, float(tau), float(tau_cap),
+                                                 int(round_index), ctypes.byref(n)))
+        return n.value
+
+    def reset_history(self):
+        _check(load_library().fm_reset_history(self._h))
+
     def set_weights(self, w):
         if _is_cuda(w):
             import torch
@@ -301,3 +338,58 @@ class Problem:
         n = ctypes.c_int64()
         _check(load_library().fm_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+
+class Mlp:
+    """The learned inlier-weight network on the GPU (fm_mlp_*): FP32 masters, BF16 copies."""
+
+    def __init__(self, params):
+        lib = load_library()
+        self.n_params = lib.fm_mlp_num_params()
+        pv = _host(params, np.float32).reshape(-1)
+        if pv.shape[0] != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        h = ctypes.c_void_p()
+        _check(lib.fm_mlp_create(_ptr(pv), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().fm_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _check(load_library().fm_mlp_get_params(self._h, _ptr(out)))
+        return out
+
+    def set_params(self, params):
+        pv = _host(params, np.float32).reshape(-1)
+        _check(load_library().fm_mlp_set_params(self._h, _ptr(pv)))
+
+    def train_step(self, feats, labels, lr: float, want_loss: bool = True, stream=None):
+        """One Adam step on CUDA tensors feats (n x 8 bfloat16) and labels (n float32)."""
+        loss = ctypes.c_float()
+        _check(load_library().fm_mlp_train_step(
+            self._h, ctypes.c_void_p(feats.data_ptr()), ctypes.c_void_p(labels.data_ptr()), int(labels.numel()),
+            float(lr), ctypes.byref(loss) if want_loss else None,
+            stream if stream is not None else _current_stream()))
+        return loss.value if want_loss else None
+
+    def gradient(self, feats, labels):
+        g = np.empty(self.n_params, np.float32)
+        loss = ctypes.c_float()
+        _check(load_library().fm_mlp_gradient(self._h, ctypes.c_void_p(feats.data_ptr()),
+                                              ctypes.c_void_p(labels.data_ptr()), int(labels.numel()),
+                                              _ptr(g), ctypes.byref(loss)))
+        return loss.value, g
+
+    def forward(self, feats, out):
+        _check(load_library().fm_mlp_forward(self._h, ctypes.c_void_p(feats.data_ptr()), int(out.numel()),
+                                             ctypes.c_void_p(out.data_ptr()), _current_stream()))

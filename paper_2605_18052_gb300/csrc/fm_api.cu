@@ -34,6 +34,7 @@ fm_status fail(fm_status s, const std::string &msg) {
 
 // lets other translation units of the library report through fm_last_error
 void fm_internal_set_error(const char *msg) { g_last_error = msg; }
+void fm_internal_mlp_params(const fm_mlp *net, const float **master, const __nv_bfloat16 **wbf);
 
 struct fm_problem {
     DevProblem d{};
@@ -44,6 +45,7 @@ struct fm_problem {
     cudaGraphExec_t graph = nullptr;      // one iteration
     cudaGraphExec_t graph8 = nullptr;     // eight chained iterations
     bool timing = false;
+    int hist_valid = 0;                   // d.le_hist holds a previous reweighting's residuals
     std::vector<cudaEvent_t> tev;   // timing events, pairs (start, end)
     size_t tev_used = 0;
     int input_was_sorted = 0;
@@ -272,6 +274,13 @@ fm_status create_impl(fm_problem *p, int32_t n_cams, const double *R, const doub
         d.kp = kp;
         d.w = w;
     }
+    FM_CUDA(dalloc(p, &d.score, (size_t)d.n_pad));
+    FM_CUDA(dalloc(p, &d.le_hist, (size_t)d.n_pad));
+    {
+        float4 *ps;
+        FM_CUDA(dalloc(p, &ps, (size_t)n_pairs));
+        d.pstat = reinterpret_cast<float *>(ps);
+    }
     FM_CUDA(dalloc(p, &d.geo, (size_t)GEO * n_pairs));
     FM_CUDA(dalloc(p, &d.slots, (size_t)SLOT * ((size_t)n_pairs + d.n_ranges)));
     FM_CUDA(dalloc(p, &d.pair_grad, (size_t)PG * n_pairs));
@@ -358,6 +367,8 @@ fm_status create_impl(fm_problem *p, int32_t n_cams, const double *R, const doub
     }
     launch_pack(d, keys, d_x1, d_x2, p->s);
     launch_fill_weights(d, 1.0f, p->s);
+    launch_fill_half(d.score, d.n_pad, 0.5f, p->s);
+    launch_fill_half(d.le_hist, d.n_pad, 0.0f, p->s);
     FM_CUDA(cudaGetLastError());
     if (sorted_keys) FM_CUDA(cudaFreeAsync(sorted_keys, p->s));
     release_temps();
@@ -559,6 +570,82 @@ FM_API fm_status fm_get_weights(fm_problem *p, float *w) {
     FM_CUDA(cudaMemcpyAsync(w, tmp, sizeof(float) * p->d.n_pp, cudaMemcpyDeviceToHost, p->s));
     FM_CUDA(cudaFreeAsync(tmp, p->s));
     FM_CUDA(cudaStreamSynchronize(p->s));
+    return FM_OK;
+}
+
+FM_API fm_status fm_set_scores(fm_problem *p, const float *score, int32_t on_device) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!score) return fail(FM_EINVAL, "score must not be NULL");
+    if (on_device != 0 && on_device != 1) return fail(FM_EINVAL, "on_device must be 0 or 1");
+    FM_CUDA(join_in(p));
+    const float *src = score;
+    float *tmp = nullptr;
+    if (!on_device) {
+        FM_CUDA(cudaMallocAsync(&tmp, sizeof(float) * p->d.n_pp, p->s));
+        FM_CUDA(cudaMemcpyAsync(tmp, score, sizeof(float) * p->d.n_pp, cudaMemcpyHostToDevice, p->s));
+        src = tmp;
+    }
+    launch_set_scores(p->d, src, p->s);
+    FM_CUDA(cudaGetLastError());
+    if (tmp) FM_CUDA(cudaFreeAsync(tmp, p->s));
+    unsigned err = 0;
+    FM_CUDA(cudaMemcpyAsync(&err, p->d.err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->s));
+    FM_CUDA(cudaStreamSynchronize(p->s));
+    if (err & ERR_WEIGHT) {
+        unsigned keep = err & ~ERR_WEIGHT;
+        FM_CUDA(cudaMemcpyAsync(p->d.err, &keep, sizeof(unsigned), cudaMemcpyHostToDevice, p->s));
+        FM_CUDA(cudaStreamSynchronize(p->s));
+        return fail(FM_EINVAL, "scores must be in [0, 1]; offending scores were set to 0.5");
+    }
+    FM_CUDA(join_out(p));
+    return FM_OK;
+}
+
+FM_API fm_status fm_reset_history(fm_problem *p) {
+    if (fm_status st = check_problem(p)) return st;
+    p->hist_valid = 0;
+    return FM_OK;
+}
+
+FM_API fm_status fm_collect_features(fm_problem *p, double tau, int32_t round, void *d_features) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!d_features) return fail(FM_EINVAL, "d_features must not be NULL");
+    if (!(tau > 0.0) || std::isinf(tau)) return fail(FM_EINVAL, "tau must be finite and > 0");
+    if (round < 0) return fail(FM_EINVAL, "round must be >= 0");
+    FM_CUDA(join_in(p));
+    launch_pair_setup(p->d, p->s);
+    launch_pair_stats(p->d, (float)tau, p->s);
+    launch_collect_features(p->d, (float)tau, round, p->hist_valid, static_cast<__nv_bfloat16 *>(d_features), p->s);
+    FM_CUDA(cudaGetLastError());
+    p->hist_valid = 1;
+    if (fm_status st = check_device_errors(p)) return st;
+    FM_CUDA(join_out(p));
+    return FM_OK;
+}
+
+FM_API fm_status fm_learned_weights(fm_problem *p, const fm_mlp *net, double tau, double tau_cap,
+                                    int32_t round, int64_t *n_active) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!net) return fail(FM_EINVAL, "net must not be NULL");
+    if (!(tau > 0.0) || std::isinf(tau)) return fail(FM_EINVAL, "tau must be finite and > 0");
+    if (std::isnan(tau_cap) || tau_cap < 0.0) return fail(FM_EINVAL, "tau_cap must be >= 0 (may be +inf)");
+    if (round < 0) return fail(FM_EINVAL, "round must be >= 0");
+    const float *master = nullptr;
+    const __nv_bfloat16 *wbf = nullptr;
+    fm_internal_mlp_params(net, &master, &wbf);
+    FM_CUDA(join_in(p));
+    FM_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(unsigned long long), p->s));
+    launch_pair_setup(p->d, p->s);
+    launch_pair_stats(p->d, (float)tau, p->s);
+    launch_learned_weights(p->d, master, wbf, (float)tau, std::isinf(tau_cap) ? INFINITY : (float)tau_cap, round,
+                           p->hist_valid, p->s);
+    FM_CUDA(cudaGetLastError());
+    p->hist_valid = 1;
+    unsigned long long cnt = 0;
+    FM_CUDA(cudaMemcpyAsync(&cnt, p->d.counter, sizeof cnt, cudaMemcpyDeviceToHost, p->s));
+    if (fm_status st = check_device_errors(p)) return st;
+    if (n_active) *n_active = (int64_t)cnt;
+    FM_CUDA(join_out(p));
     return FM_OK;
 }
 

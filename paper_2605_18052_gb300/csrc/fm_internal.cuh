@@ -1,6 +1,7 @@
 // Internal layout and kernel declarations of libfastmap (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -74,7 +75,31 @@ struct DevProblem {
     unsigned *err;
     unsigned long long *counter;
     float *fbuf;            // n_pad floats of scratch (residual export)
+    // learned inlier weights
+    __half *score;          // per point pair: matcher confidence (0.5 until set)
+    __half *le_hist;        // per point pair: log(|eps| + 1e-6) at the previous reweighting
+    float *pstat;           // per pair: mean log residual, inlier fraction, log(count)/10, 0
 };
+
+// ---- learned inlier-weight MLP (fm_mlp.cu) ------------------------------------------------------
+constexpr int MLP_IN = 8;
+constexpr int MLP_H = 32;
+constexpr int MLP_OFF_W1 = 0;                                // W1[k][n], 8 x 32
+constexpr int MLP_OFF_B1 = MLP_OFF_W1 + MLP_IN * MLP_H;      // 32
+constexpr int MLP_OFF_W2 = MLP_OFF_B1 + MLP_H;               // W2[k][n], 32 x 32
+constexpr int MLP_OFF_B2 = MLP_OFF_W2 + MLP_H * MLP_H;       // 32
+constexpr int MLP_OFF_W3 = MLP_OFF_B2 + MLP_H;               // W3[k], 32
+constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_H;               // 1
+constexpr int MLP_NPARAM = MLP_OFF_B3 + 1;                   // 1377
+constexpr float LOG_FLOOR = 1e-6f;
+
+// pair statistics of the current residuals (pstat), then features -> MLP -> weights, or the
+// features themselves (input order) for training
+void launch_pair_stats(const DevProblem &d, float tau, cudaStream_t s);
+void launch_learned_weights(const DevProblem &d, const float *mlp_master, const __nv_bfloat16 *mlp_bf16,
+                            float tau, float tau_cap, int round, int hist_valid, cudaStream_t s);
+void launch_collect_features(const DevProblem &d, float tau, int round, int hist_valid,
+                             __nv_bfloat16 *feat_input_order, cudaStream_t s);
 
 // ---- kernels launched by the API layer (fm_kernels.cu) ----------------------------------------
 void launch_cam_prep(const DevProblem &d, cudaStream_t s);
@@ -118,5 +143,8 @@ void launch_set_weights(const DevProblem &d, const float *w_input_order, cudaStr
 void launch_get_weights(const DevProblem &d, float *w_input_order, cudaStream_t s);
 void launch_unpermute(const DevProblem &d, const float *sorted, float *input_order,
                       cudaStream_t s);
+void launch_fill_half(__half *p, int64_t n, float value, cudaStream_t s);
+// match scores in input order -> d.score (sorted order, FP16); values outside [0, 1] -> ERR_WEIGHT
+void launch_set_scores(const DevProblem &d, const float *score_input_order, cudaStream_t s);
 
 }  // namespace fm

@@ -398,4 +398,26 @@ void launch_unpermute(const DevProblem &d, const float *sorted, float *input_ord
     k_unpermute<<<blocks_for(d.n_pp, 256), 256, 0, s>>>(d.perm, d.n_pp, sorted, input_order);
 }
 
+__global__ void k_fill_half(__half *p, int64_t n, float value) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) p[q] = __float2half_rn(value);
+}
+
+void launch_fill_half(__half *p, int64_t n, float value, cudaStream_t s) {
+    k_fill_half<<<blocks_for(n, 256), 256, 0, s>>>(p, n, value);
+}
+
+__global__ void k_set_scores(DevProblem d, const float *score_in) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= d.n_pp) return;
+    const float v = score_in[d.perm ? d.perm[q] : q];
+    const bool ok = v >= 0.f && v <= 1.f;  // false for NaN
+    if (!ok) atomicOr(d.err, ERR_WEIGHT);
+    d.score[q] = __float2half_rn(ok ? v : 0.5f);
+}
+
+void launch_set_scores(const DevProblem &d, const float *score_input_order, cudaStream_t s) {
+    k_set_scores<<<blocks_for(d.n_pp, 256), 256, 0, s>>>(d, score_input_order);
+}
+
 }  // namespace fm

@@ -1,0 +1,119 @@
+"""The learned inlier-weight kernels against the oracle: SIMT forward and training gradient,
+the tensor-core inference inside the streaming pass, the per-point-pair features, and that
+training with the library's kernels reduces the loss.
+
+Tolerances: both sides use BF16 inputs, weights and hidden activations; they differ in the
+FP32 summation order of each dot product and, rarely, in a hidden activation that lands on
+the other side of a BF16 rounding boundary, which moves p by a few 1e-3 at most. Features
+are computed in FP32 on the GPU (FP64 in the oracle) from residuals that differ by the FP32
+forward error (2e-6, see test_gpu_parity), so they are compared where |eps| >= 1e-3 (a
+relative residual error below 2e-3) and up to BF16 rounding; the history is stored in FP16.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import learned as L
+import scenegen
+import paper_2605_18052_gb300 as fm
+from paper_2605_18052_gb300 import build, learned
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    build.build()
+    fm.load_library()
+
+
+def _params(seed):
+    v = learned.init_params(seed)
+    rng = np.random.default_rng(seed + 100)
+    return (v + 0.05 * rng.normal(size=v.shape)).astype(np.float32)
+
+
+def test_forward_and_gradient_match_oracle():
+    rng = np.random.default_rng(0)
+    n = 5000
+    X = L.bf16_round(rng.normal(0, 2, (n, 8)))
+    y = (rng.random(n) < 0.6).astype(np.float32)
+    pv = _params(1)
+    net = fm.Mlp(pv)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda").to(torch.bfloat16)
+    Yd = torch.tensor(y, device="cuda")
+    p_gpu = torch.empty(n, dtype=torch.float32, device="cuda")
+    net.forward(Xd, p_gpu)
+    torch.cuda.synchronize()
+    params = L.unflatten(pv.astype(np.float64))
+    p_or = L.forward_bf16(params, X)
+    assert np.abs(p_gpu.cpu().numpy() - p_or).max() < 5e-3
+    loss, g = net.gradient(Xd, Yd)
+    l_or, g_or = L.bce_loss_grad_bf16(params, X, y.astype(np.float64))
+    g_or = L.flatten(g_or)
+    assert loss == pytest.approx(l_or, rel=1e-3)
+    assert np.abs(g - g_or).max() <= 2e-3 * np.abs(g_or).max()
+
+
+def test_training_reduces_loss():
+    rng = np.random.default_rng(2)
+    n = 40000
+    X = rng.normal(0, 1, (n, 8))
+    y = ((X[:, 0] + 0.5 * X[:, 3] - 0.3 * X[:, 5] ** 2) > 0).astype(np.float32)
+    net = fm.Mlp(learned.init_params(3))
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda").to(torch.bfloat16)
+    Yd = torch.tensor(y, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    losses = learned.train(net, Xd, Yd, 400, 4096, 3e-3, g, log_every=100)
+    assert losses[-1][1] < 0.35 * losses[0][1]
+    p = torch.empty(n, dtype=torch.float32, device="cuda")
+    net.forward(Xd, p)
+    acc = ((p.cpu().numpy() > 0.5) == (y > 0.5)).mean()
+    assert acc > 0.95
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_features_and_learned_weights_match_oracle(storage):
+    sc = scenegen.make_scene("sphere128", seed=5)
+    R0, t0 = sc.R_init.numpy(), sc.t_init.numpy()
+    c0 = O.centres_from_poses(R0, t0)
+    prob = O.Problem.from_scene(sc)
+    if storage == "fp16":
+        _, d1, d2 = O.fp16_centroid_storage(prob, sc.x1.numpy(), sc.x2.numpy())
+        prob = O.Problem(sc.n_cams, prob.cam_i, prob.cam_j, prob.pair_id, d1, d2)
+    score = sc.score.numpy()
+    tau0, tau1 = 0.3, 0.2
+    pv = _params(7)
+    net = fm.Mlp(pv)
+    feats = torch.empty(sc.n_pp, 8, dtype=torch.bfloat16, device="cuda")
+    with fm.Problem(R0, t0, sc.cam_i, sc.cam_j, sc.pair_id, sc.x1, sc.x2,
+                    options=fm.default_options(storage=storage)) as gp:
+        gp.set_scores(score)
+        gp.collect_features(tau0, 0, feats)          # round 0: history = current residuals
+        f0 = feats.to(torch.float32).cpu().numpy()
+        gp.step(5)                                    # move the poses
+        R5, c5 = gp.get_params()
+        kept = gp.learned_weights(net, tau1, tau1, 1)  # round 1, history from round 0
+        w_gpu = gp.get_weights().astype(np.float64)
+    e0 = np.abs(O.residuals(prob, R0, c0))
+    e5 = np.abs(O.residuals(prob, R5, c5))
+    sc16 = score.astype(np.float16).astype(np.float64)
+    F0 = L.features(e0, e0, sc16, prob.pair_id, prob.n_pairs, tau0, 0)
+    ok = e0 >= 1e-3
+    assert ok.mean() > 0.5
+    d = np.abs(f0 - L.bf16_round(F0))[ok]
+    tol = 2 ** -7 * np.abs(F0[ok]) + 2e-2
+    assert (d <= tol).mean() > 0.999
+    # learned weights at round 1 with the round-0 residuals as history (stored in FP16)
+    hist = np.log(e0 + 1e-6).astype(np.float16).astype(np.float64)
+    F1 = L.features(e5, np.exp(hist) - 1e-6, sc16, prob.pair_id, prob.n_pairs, tau1, 1)
+    w_or, p_or = L.learned_weights(L.unflatten(pv.astype(np.float64)), e5, F1, 1e-6, tau_cap=tau1)
+    ok1 = (e5 >= 1e-3) & (e5 <= 0.9 * tau1)
+    rel = np.abs(w_gpu[ok1] - w_or[ok1]) / np.maximum(w_or[ok1], 1e-12)
+    assert np.median(rel) < 1e-2
+    assert (rel < 0.1).mean() > 0.99
+    assert abs(kept - (e5 <= tau1).sum()) <= 0.001 * sc.n_pp

@@ -48,6 +48,12 @@ def test_build_flags_target_sm_103a():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
+def test_public_python_surface():
+    for name in ["Problem", "Mlp", "Schedule", "refine", "epipolar_loss", "EpipolarLoss", "default_options"]:
+        assert hasattr(fm, name), name
+    from paper_2605_18052_gb300 import learned, metrics  # noqa: F401
+
+
 def test_default_options(lib):
     o = fm.default_options()
     assert (o.storage, o.loss, o.delta, o.beta1, o.beta2, o.use_graph) == (0, 0, 1e-6, 0.9, 0.999, 1)
