@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-tta", action="store_true", help="skip the time-to-accuracy comparison")
+    ap.add_argument("--tta-config", default="traj1000_o30")
+    ap.add_argument("--tta-rounds", type=int, default=120)
     return ap.parse_args()
 
 
@@ -124,14 +127,36 @@ class ClockSampler:
 
 
 def schedule_for(sc, iters):
+    from paper_2605_18052_gb300.learned import default_schedule
+    return default_schedule(sc, max(1, sc.iters // iters), iters)
+
+
+def time_to_accuracy_section(args):
+    """Learned vs plain IRLS: device time to mean rotation error <= 0.1 deg on the 1,000-camera
+    scene with 30% outliers (the evaluation scene of the learned-weight workload)."""
     import numpy as np
-    from paper_2605_18052_gb300 import Schedule
-    R, t = sc.R_gt.double(), sc.t_gt.double()
-    C = -(R.transpose(1, 2) @ t[:, :, None])[:, :, 0]
-    base = float((C[sc.cam_i.long()] - C[sc.cam_j.long()]).norm(dim=1).median())
-    rounds = max(1, sc.iters // iters)
-    return Schedule(rounds=rounds, iters_per_round=iters, tau0=0.5, tau_min=4 * sc.sigma_px / sc.f,
-                    tau_factor=0.8, decay=0.95, lr_rot=1e-2, lr_c=1e-2 * base)
+    import torch
+    import scenegen
+    from paper_2605_18052_gb300 import Mlp, learned
+    path = os.path.join(ROOT, "paper_2605_18052_gb300", "data", "mlp_inlier.npy")
+    if not os.path.exists(path):
+        return {"unavailable": "no trained network (python -m paper_2605_18052_gb300.learned)"}
+    sc = scenegen.make_scene(args.tta_config, seed=args.seed, device="cuda")
+    torch.cuda.empty_cache()
+    net = Mlp(np.load(path))
+    out = {"scene": f"{args.tta_config}: {sc.n_cams} cameras, {sc.n_pp} point pairs",
+           "threshold_deg": 0.1, "storage": args.storage}
+    for arm in ("irls", "learned"):
+        r = learned.time_to_accuracy(sc, arm, net if arm == "learned" else None, args.storage, args.tta_rounds)
+        out[arm] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items() if k != "history_deg"}
+        out[arm]["history_deg_every_5"] = [round(x, 4) for x in r["history_deg"][::5]]
+    if out["irls"]["reached"] and out["learned"]["reached"]:
+        out["speedup_learned_over_irls"] = out["irls"]["ms"] / out["learned"]["ms"]
+    else:
+        out["speedup_learned_over_irls"] = None
+        out["note"] = "0.1 deg not reached by both arms within the round budget; see ms_to per threshold"
+    net.close()
+    return out
 
 
 def cpu_oracle_rate(sc, seconds: float):
@@ -306,6 +331,10 @@ def main():
                "seconds_per_job": t_job,
                "seconds_create_refine_destroy": [round(statistics.median(x[i] for x in parts[1:]), 5) for i in range(3)]}
 
+    tta = None
+    if rank == 0 and not args.no_tta:
+        tta = time_to_accuracy_section(args)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, sample = cpu_oracle_rate(sc, args.cpu_seconds)
@@ -322,6 +351,7 @@ def main():
                           "l2": "inputs larger than L2 (no flush needed)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "time_to_accuracy": tta,
                "clocks": clocks, "hbm_frac_of_step": value * 1e9 * bytes_per_launch / n_pp / 1e9 / peak}
         print(json.dumps(out))
     if world > 1:

@@ -31,7 +31,7 @@ struct StatsBody {
     __device__ __forceinline__ void segment_begin(int) {}
     __device__ __forceinline__ void point(int, float e, float, float, float, float, float) {
         const float a = fabsf(e);
-        acc[0] += logf(a + LOG_FLOOR);
+        acc[0] += __logf(a + LOG_FLOOR);
         acc[1] += a <= tau ? 1.f : 0.f;
     }
     __device__ __forceinline__ void segment_end(int seg, int r, int lane, bool) {
@@ -168,8 +168,8 @@ __device__ __forceinline__ void mlp_tiles(const MlpFrag &f, const __nv_bfloat16 
         mma_bf16(z, a3[0], f.w3[0][0], f.w3[0][1]);
         mma_bf16(z, a3[1], f.w3[1][0], f.w3[1][1]);
         if (t == 0) {
-            ps[r0] = 1.f / (1.f + expf(-z[0]));
-            ps[r1] = 1.f / (1.f + expf(-z[2]));
+            ps[r0] = __frcp_rn(1.f + __expf(-z[0]));
+            ps[r1] = __frcp_rn(1.f + __expf(-z[2]));
         }
     }
 }
@@ -201,7 +201,7 @@ struct LearnedBody {
     }
     __device__ __forceinline__ void point(int k, float e, float, float, float, float, float) {
         ae[k] = fabsf(e);
-        le[k] = logf(ae[k] + LOG_FLOOR);
+        le[k] = __logf(ae[k] + LOG_FLOOR);
         sm[k] = st_mean;
         sf[k] = st_frac;
         sc[k] = st_cnt;
@@ -265,22 +265,23 @@ struct LearnedBody {
 };
 
 template <int STORE, bool COLLECT>
-__global__ void __launch_bounds__(CTA_WARPS * 32)
+__global__ void __launch_bounds__(CTA_WARPS * 32, 2)
 k_learned(DevProblem d, const float *master, const __nv_bfloat16 *wbf, float tau, float tau_cap,
           int round, int hist_valid, __nv_bfloat16 *feat_out) {
     constexpr int GROUP = 32 * Fmt<STORE>::PPL;
     __shared__ __align__(16) __nv_bfloat16 xs[CTA_WARPS][GROUP][MLP_IN];
     __shared__ float ps[CTA_WARPS][GROUP];
+    __shared__ MlpFrag sfrag[32];   // per-lane fragments, shared by the CTA's warps
     __shared__ unsigned cta_kept;
     if (threadIdx.x == 0) cta_kept = 0;
-    __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (!COLLECT && w == 0) load_frag(sfrag[lane], master, wbf, lane);
+    __syncthreads();
     const int r = blockIdx.x * CTA_WARPS + w;
-    MlpFrag frag;
-    if (!COLLECT) load_frag(frag, master, wbf, lane);
+    const MlpFrag &frag = sfrag[lane];
     if (r < d.n_ranges) {
         LearnedBody<STORE, COLLECT> body(d);
-        body.log_tau = logf(tau);
+        body.log_tau = __logf(tau);
         body.tau_cap = tau_cap;
         body.delta = (float)d.delta;
         body.wscale = d.w_scale;

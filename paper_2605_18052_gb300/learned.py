@@ -78,3 +78,118 @@ def refine_learned(problem, net: Mlp, schedule: Schedule, callback=None, first_r
         if callback is not None:
             callback(r, problem)
     return problem
+
+
+# ---- training on the method's own converged runs ------------------------------------------------
+def default_schedule(sc, rounds: int, iters: int = 25) -> Schedule:
+    """The plain-IRLS schedule used for both arms (see the design notes for the readings)."""
+    R, t = sc.R_gt.double(), sc.t_gt.double()
+    C = -(R.transpose(1, 2) @ t[:, :, None])[:, :, 0]
+    base = float((C[sc.cam_i.long()] - C[sc.cam_j.long()]).norm(dim=1).median())
+    return Schedule(rounds=rounds, iters_per_round=iters, tau0=0.5, tau_min=4 * sc.sigma_px / sc.f,
+                    tau_factor=0.8, decay=0.95, lr_rot=1e-2, lr_c=1e-2 * base)
+
+
+def train_from_scenes(config: str, seeds, rounds: int, collect_rounds: int, per_round: int,
+                      steps: int, batch: int, lr: float, seed: int = 0, log=print):
+    """Collect training data from plain-IRLS runs on seeded scenes of `config` and train a
+    network with the library's kernels. Returns the trained parameters (flat float32)."""
+    import scenegen
+    from .binding import Problem, default_options
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    Xs, Ys = [], []
+    for k, s in enumerate(seeds):
+        sc = scenegen.make_scene(config, seed=int(s), device="cuda")
+        sch = default_schedule(sc, rounds)
+        with Problem(sc.R_init.cpu(), sc.t_init.cpu(), sc.cam_i.cpu(), sc.cam_j.cpu(), sc.pair_id,
+                     sc.x1, sc.x2, options=default_options(lr_rot=sch.lr_rot, lr_c=sch.lr_c)) as gp:
+            gp.set_scores(sc.score)
+            X, Y = collect_training_data(gp, sch, collect_rounds, per_round, gen)
+        Xs.append(X)
+        Ys.append(Y)
+        if log and (k % 20 == 0 or k == len(seeds) - 1):
+            log(f"scene {k + 1}/{len(seeds)} seed {s}: {sc.n_pp} point pairs, inlier labels {float(Y.mean()):.3f}")
+        del sc
+        torch.cuda.empty_cache()
+    X = torch.cat(Xs)
+    Y = torch.cat(Ys)
+    net = Mlp(init_params(seed))
+    losses = train(net, X, Y, steps, batch, lr, gen, log_every=max(1, steps // 10))
+    if log:
+        log("training losses: " + ", ".join(f"{it}:{l:.4f}" for it, l in losses))
+    out = net.params()
+    net.close()
+    return out, X.shape[0], losses
+
+
+def time_to_accuracy(sc, arm: str, net: Mlp | None = None, storage: str = "fp16", max_rounds: int = 80,
+                     threshold_deg: float = 0.1, thresholds=(2.0, 1.0, 0.5, 0.25, 0.1)):
+    """Device time of the refinement loop until the mean rotation error (after global
+    alignment) is <= threshold_deg, and the time at which each of `thresholds` was first
+    reached. The error is checked after every round and the check is not timed.
+    arm: "irls" (plain reweighting) or "learned". Returns a dict."""
+    from . import metrics
+    from .binding import Problem, default_options
+    sch = default_schedule(sc, max_rounds)
+    Rg = sc.R_gt.cpu().numpy()
+    stream = torch.cuda.current_stream()
+    total_ms, hist, first = 0.0, [], {}
+    with Problem(sc.R_init.cpu(), sc.t_init.cpu(), sc.cam_i.cpu(), sc.cam_j.cpu(), sc.pair_id, sc.x1, sc.x2,
+                 options=default_options(storage=storage, lr_rot=sch.lr_rot, lr_c=sch.lr_c)) as gp:
+        gp.set_scores(sc.score)
+        gp.reset_history()
+        for r in range(max_rounds):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            tau = sch.tau(r)
+            if arm == "irls":
+                gp.irls_weights(tau)
+            else:
+                gp.learned_weights(net, tau, tau, r)
+            s = sch.decay ** r
+            gp.set_learning_rate(sch.lr_rot * s, sch.lr_c * s)
+            gp.step(sch.iters_per_round)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            R, _ = gp.get_poses()
+            err = float(metrics.rotation_error_deg(R, Rg).mean())
+            hist.append(err)
+            for th in thresholds:
+                if err <= th and th not in first:
+                    first[th] = (total_ms, r + 1)
+            if err <= threshold_deg:
+                break
+    done = hist[-1] <= threshold_deg
+    return {"reached": done, "ms": total_ms, "rounds": len(hist), "final_deg": hist[-1], "history_deg": hist,
+            "ms_to": {str(th): (round(first[th][0], 3) if th in first else None) for th in thresholds},
+            "rounds_to": {str(th): (first[th][1] if th in first else None) for th in thresholds}}
+
+
+def _main():
+    import argparse
+    import os
+    ap = argparse.ArgumentParser(description="train the inlier-weight MLP on converged IRLS runs")
+    ap.add_argument("--config", default="sphere128")
+    ap.add_argument("--scenes", type=int, default=200)
+    ap.add_argument("--first-seed", type=int, default=1000)
+    ap.add_argument("--rounds", type=int, default=40)
+    ap.add_argument("--collect-rounds", type=int, default=6)
+    ap.add_argument("--per-round", type=int, default=8192)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "mlp_inlier.npy"))
+    a = ap.parse_args()
+    params, n, losses = train_from_scenes(a.config, range(a.first_seed, a.first_seed + a.scenes), a.rounds,
+                                          a.collect_rounds, a.per_round, a.steps, a.batch, a.lr)
+    os.makedirs(os.path.dirname(a.out), exist_ok=True)
+    np.save(a.out, params)
+    print(f"saved {a.out}: {params.shape[0]} parameters trained on {n} samples")
+
+
+if __name__ == "__main__":
+    _main()
