@@ -92,8 +92,10 @@ typedef struct {
     double lr_c;         /* Adam step size for camera centres (scene units) */
     double beta1, beta2; /* Adam moment decay rates, in [0, 1) */
     double adam_eps;     /* Adam denominator epsilon, >= 0 */
-    int32_t use_graph;   /* 1: replay one captured CUDA graph per iteration in fm_step */
+    int32_t use_graph;   /* 1: replay captured CUDA graphs of chained iterations in fm_step */
     int32_t reserved;    /* must be 0 */
+    int64_t z_total;     /* Z of the objective; 0 means n_pp. A shard of a problem split across
+                            processes sets the total point-pair count of all shards. */
 } fm_options;
 
 typedef struct {
@@ -186,6 +188,13 @@ FM_API fm_status fm_step(fm_problem *p, int32_t n_iters);
 
 /* Objective value of the most recent iteration of fm_step (or fm_loss_grad). Synchronises. */
 FM_API fm_status fm_last_loss(fm_problem *p, double *loss);
+
+/*
+ * One optimiser step with a gradient computed elsewhere (for example the sum of the gradients
+ * of a problem's shards on several processes): grad is n_cams x 6 FP64, host, or device when
+ * on_device is 1. Same update as one fm_step iteration. Synchronises.
+ */
+FM_API fm_status fm_apply_gradient(fm_problem *p, const double *grad, int32_t on_device);
 
 /* Change the Adam step sizes used by later iterations (a learning-rate schedule). */
 FM_API fm_status fm_set_learning_rate(fm_problem *p, double lr_rot, double lr_c);

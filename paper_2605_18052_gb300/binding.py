@@ -21,7 +21,7 @@ EXPORTED = [
     "fm_get_poses", "fm_set_poses", "fm_get_params", "fm_set_params", "fm_set_params_device", "fm_set_weights", "fm_get_weights", "fm_irls_weights",
     "fm_loss_grad", "fm_loss_grad_device", "fm_residuals", "fm_step", "fm_last_loss",
     "fm_set_learning_rate", "fm_reset_optimizer", "fm_get_state", "fm_set_state",
-    "fm_synchronize", "fm_enable_kernel_timing", "fm_kernel_time", "fm_loss_grad_noalloc",
+    "fm_synchronize", "fm_apply_gradient", "fm_enable_kernel_timing", "fm_kernel_time", "fm_loss_grad_noalloc",
     "fm_status_string", "fm_last_error", "fm_mlp_num_params", "fm_mlp_create", "fm_mlp_destroy",
     "fm_mlp_get_params", "fm_mlp_set_params", "fm_mlp_train_step", "fm_mlp_gradient", "fm_mlp_forward",
     "fm_set_scores", "fm_collect_features", "fm_learned_weights", "fm_reset_history",
@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("loss", ctypes.c_int32), ("delta", ctypes.c_double),
                 ("lr_rot", ctypes.c_double), ("lr_c", ctypes.c_double), ("beta1", ctypes.c_double),
                 ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32), ("z_total", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "fm_get_state": (I32, [P, P, P, P]),
         "fm_set_state": (I32, [P, P, P, I64]),
         "fm_synchronize": (I32, [P]),
+        "fm_apply_gradient": (I32, [P, P, I32]),
         "fm_enable_kernel_timing": (I32, [P, I32]),
         "fm_kernel_time": (I32, [P, P, P]),
         "fm_loss_grad_noalloc": (I32, [I32, P, P, I32, P, P, P, I64, P, P, I32, P, P, P]),
@@ -318,6 +319,16 @@ class Problem:
         e = np.empty(self.n_pp, np.float32)
         _check(load_library().fm_residuals(self._h, _ptr(e)))
         return e
+
+    def apply_gradient(self, grad):
+        """One Adam step with a gradient computed elsewhere (n_cams x 6 float64, host or CUDA)."""
+        if _is_cuda(grad):
+            import torch
+            g = grad.to(torch.float64).contiguous()
+            _check(load_library().fm_apply_gradient(self._h, ctypes.c_void_p(g.data_ptr()), 1))
+        else:
+            g = _host(grad, np.float64)
+            _check(load_library().fm_apply_gradient(self._h, _ptr(g), 0))
 
     def step(self, n_iters: int = 1):
         _check(load_library().fm_step(self._h, int(n_iters)))

@@ -147,6 +147,7 @@ fm_status check_options(const fm_options *o) {
         return fail(FM_EINVAL, "beta1 and beta2 must be in [0, 1)");
     if (!(o->adam_eps >= 0.0) || !std::isfinite(o->adam_eps)) return fail(FM_EINVAL, "adam_eps must be >= 0");
     if (o->reserved != 0) return fail(FM_EINVAL, "reserved must be 0");
+    if (o->z_total < 0) return fail(FM_EINVAL, "z_total must be >= 0");
     return FM_OK;
 }
 
@@ -221,6 +222,7 @@ fm_status create_impl(fm_problem *p, int32_t n_cams, const double *R, const doub
     d.storage = p->opt.storage;
     d.loss = p->opt.loss;
     d.delta = p->opt.delta;
+    d.z = p->opt.z_total > 0 ? (double)p->opt.z_total : (double)n_pp;
     d.w_scale = 1.0f;
     if (d.storage == FM_STORE_FP16) d.w_scale = (float)std::exp2(std::floor(std::log2(32768.0 * p->opt.delta)));
 
@@ -406,6 +408,7 @@ FM_API void fm_default_options(fm_options *o) {
     o->adam_eps = 1e-12;
     o->use_graph = 1;
     o->reserved = 0;
+    o->z_total = 0;
 }
 
 FM_API fm_status fm_create_problem(int32_t n_cams, const double *R, const double *t,
@@ -744,6 +747,21 @@ FM_API fm_status fm_last_loss(fm_problem *p, double *loss) {
     FM_CUDA(join_in(p));
     FM_CUDA(cudaMemcpyAsync(loss, p->d.loss_out, sizeof(double), cudaMemcpyDeviceToHost, p->s));
     return check_device_errors(p);
+}
+
+FM_API fm_status fm_apply_gradient(fm_problem *p, const double *grad, int32_t on_device) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!grad) return fail(FM_EINVAL, "grad must not be NULL");
+    if (on_device != 0 && on_device != 1) return fail(FM_EINVAL, "on_device must be 0 or 1");
+    if (!on_device && !finite_all(grad, 6 * (size_t)p->d.n_cams)) return fail(FM_EINVAL, "gradient must be finite");
+    FM_CUDA(join_in(p));
+    FM_CUDA(cudaMemcpyAsync(p->d.grad, grad, sizeof(double) * 6 * p->d.n_cams,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->s));
+    launch_apply_gradient(p->d, p->s);
+    FM_CUDA(cudaGetLastError());
+    FM_CUDA(cudaStreamSynchronize(p->s));
+    FM_CUDA(join_out(p));
+    return FM_OK;
 }
 
 FM_API fm_status fm_set_learning_rate(fm_problem *p, double lr_rot, double lr_c) {

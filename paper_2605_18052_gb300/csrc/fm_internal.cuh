@@ -57,6 +57,7 @@ struct DevProblem {
     int n_ranges;
     int storage, loss;
     double delta;
+    double z;               // Z of the objective (n_pp, or the total over all shards)
     float w_scale;          // FP16 weight scale s (1 for FP32 storage)
     // poses (FP64) and Adam moments (FP32)
     double *R, *c, *hyper;   // hyper: lr_rot, lr_c, beta1, beta2, eps
@@ -116,6 +117,8 @@ void launch_combine(const DevProblem &d, cudaStream_t s);
 void launch_gather(const DevProblem &d, bool count_step, cudaStream_t s);
 // fused per-camera step: combine this camera's pair partials, chain rule, FP64 sum, Adam,
 // exponential map, camera record; the last block sums the loss and advances the step count
+// Adam step of every camera with the gradient in d.grad (FP64, n_cams x 6); advances the step
+void launch_apply_gradient(const DevProblem &d, cudaStream_t s);
 // apply = false computes the gradient and loss only (no Adam step, no step count)
 void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl = false);
 void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s);

@@ -720,6 +720,54 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
     }
 }
 
+// Adam step with a given gradient (d.grad), one camera per thread: FP32 moments, FP64
+// exponential map, re-orthonormalisation and centre update; thread 0 advances the step.
+__global__ void k_apply_gradient(DevProblem d) {
+    const int kc = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long t_step = *d.step + 1;
+    if (kc < d.n_cams) {
+        const float b1 = (float)d.hyper[2], b2 = (float)d.hyper[3], eps = (float)d.hyper[4];
+        const float lr_r = (float)d.hyper[0], lr_c = (float)d.hyper[1];
+        const float bc1 = 1.f - powf(b1, (float)t_step), bc2 = 1.f - powf(b2, (float)t_step);
+        double dl[6], Rk[9], ck[3];
+        float mo[6], vo[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const size_t o = (size_t)kc * 6 + q;
+            const float gq = (float)d.grad[o];
+            mo[q] = b1 * d.m[o] + (1.f - b1) * gq;
+            vo[q] = b2 * d.v[o] + (1.f - b2) * gq * gq;
+            dl[q] = (double)(-(q < 3 ? lr_r : lr_c) * (mo[q] / bc1) / (sqrtf(vo[q] / bc2) + eps));
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Rk[q] = d.R[(size_t)kc * 9 + q];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) ck[q] = d.c[(size_t)kc * 3 + q];
+        double Ex[9], Rn[9], cn[3];
+        expmap64(dl, Ex);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Rn[3 * r + c] = Ex[3 * r] * Rk[c] + Ex[3 * r + 1] * Rk[3 + c] + Ex[3 * r + 2] * Rk[6 + c];
+        orthonormalize_rows(Rn);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cn[q] = ck[q] + dl[3 + q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            d.m[(size_t)kc * 6 + q] = mo[q];
+            d.v[(size_t)kc * 6 + q] = vo[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d.R[(size_t)kc * 9 + q] = Rn[q];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) d.c[(size_t)kc * 3 + q] = cn[q];
+        write_camrec(d.cam + (size_t)kc * CAMREC, Rn, cn);
+    }
+}
+
+__global__ void k_bump_step(DevProblem d) { *d.step += 1; }
+
 // Loss total of a camera-step launch (FP64, fixed order over its blocks) and, after an
 // optimiser step, the step count. One block.
 constexpr int FIN_THREADS = 256;
@@ -776,7 +824,7 @@ void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl) {
 }
 
 void launch_combine(const DevProblem &d, cudaStream_t s) {
-    const double Z = (double)d.n_pp;
+    const double Z = d.z > 0.0 ? d.z : (double)d.n_pp;
     float gscale, lscale;
     if (d.loss == FM_LOSS_IRLS) {  // stored weights are w * s
         gscale = (float)(2.0 / (Z * d.w_scale));
@@ -793,7 +841,7 @@ void launch_gather(const DevProblem &d, bool count_step, cudaStream_t s) {
 }
 
 static void loss_scales(const DevProblem &d, float &gscale, float &lscale) {
-    const double Z = (double)d.n_pp;
+    const double Z = d.z > 0.0 ? d.z : (double)d.n_pp;
     if (d.loss == FM_LOSS_IRLS) {  // stored weights are w * s
         gscale = (float)(2.0 / (Z * d.w_scale));
         lscale = (float)(1.0 / (Z * d.w_scale));
@@ -801,6 +849,11 @@ static void loss_scales(const DevProblem &d, float &gscale, float &lscale) {
         gscale = (float)(1.0 / Z);
         lscale = (float)(1.0 / Z);
     }
+}
+
+void launch_apply_gradient(const DevProblem &d, cudaStream_t s) {
+    k_apply_gradient<<<blocks_for(d.n_cams, 64), 64, 0, s>>>(d);
+    k_bump_step<<<1, 1, 0, s>>>(d);
 }
 
 void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl) {
