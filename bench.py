@@ -146,14 +146,15 @@ def time_to_accuracy_section(args):
     net = Mlp(np.load(path))
     out = {"scene": f"{args.tta_config}: {sc.n_cams} cameras, {sc.n_pp} point pairs",
            "threshold_deg": 0.1, "storage": args.storage}
-    for arm in ("irls", "learned"):
-        r = learned.time_to_accuracy(sc, arm, net if arm == "learned" else None, args.storage, args.tta_rounds)
+    for arm in ("irls", "learned", "irls_quad", "learned_quad"):
+        r = learned.time_to_accuracy(sc, arm, net if arm.startswith("learned") else None, args.storage,
+                                     args.tta_rounds)
         out[arm] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items() if k != "history_deg"}
         out[arm]["history_deg_every_5"] = [round(x, 4) for x in r["history_deg"][::5]]
-    if out["irls"]["reached"] and out["learned"]["reached"]:
-        out["speedup_learned_over_irls"] = out["irls"]["ms"] / out["learned"]["ms"]
-    else:
-        out["speedup_learned_over_irls"] = None
+    for a, b in (("irls", "learned"), ("irls_quad", "learned_quad")):
+        key = f"speedup_{b}_over_{a}"
+        out[key] = out[a]["ms"] / out[b]["ms"] if out[a]["reached"] and out[b]["reached"] else None
+    if out["speedup_learned_over_irls"] is None:
         out["note"] = "0.1 deg not reached by both arms within the round budget; see ms_to per threshold"
     net.close()
     return out

@@ -211,6 +211,30 @@ FM_API fm_status fm_reset_optimizer(fm_problem *p);
 FM_API fm_status fm_get_state(fm_problem *p, double *m, double *v, int64_t *step);
 FM_API fm_status fm_set_state(fm_problem *p, const double *m, const double *v, int64_t step);
 
+/* ---- pre-aggregated quadratic form (Eq. epipolar-objective-l2 with the IRLS weights) ---------
+ * With the weights held fixed, the objective of image pair n is quadratic in the 9 entries
+ * e_n = vec(E_n) of its essential matrix, with eps = a^T e_n and a = vec(x2 x1^T). One pass over
+ * the point pairs collects, per image pair, the weighted second moments anchored at the
+ * essential matrix e0 of the poses of that pass:
+ *   c0 = sum w eps0^2,  g0 = sum w eps0 a,  W = sum w a a^T   (FP32, 64 floats per pair)
+ * and every later evaluation costs O(1) per image pair, independent of its point-pair count:
+ *   objective = c0 + 2 d^T g0 + d^T W d,   d/de = 2 (g0 + W d),   d = e_n - e0.
+ * Within FP32 rounding this is the IRLS objective of fm_loss_grad with the weights of the
+ * pass; it goes stale when the weights change (fm_set_weights, fm_irls_weights,
+ * fm_learned_weights), and the calls below then return FM_EINVAL. Needs opt.loss ==
+ * FM_LOSS_IRLS. The device memory (about 224 B per 2048 point pairs and 320 B per image pair)
+ * is allocated by the first call.
+ */
+/* Collect the form at the current poses with the current weights. Asynchronous. */
+FM_API fm_status fm_preaggregate(fm_problem *p);
+/* fm_irls_weights(tau) and fm_preaggregate in one pass over the point pairs (the weights are
+ * written and, for FP16 storage, quantised before they enter the sums). Synchronises. */
+FM_API fm_status fm_irls_preaggregate(fm_problem *p, double tau, int64_t *n_active);
+/* Objective and gradient from the form, as fm_loss_grad (host outputs; grad may be NULL). */
+FM_API fm_status fm_loss_grad_quadratic(fm_problem *p, double *loss, double *grad);
+/* n_iters optimiser iterations of fm_step with the gradient taken from the form. Asynchronous. */
+FM_API fm_status fm_step_quadratic(fm_problem *p, int32_t n_iters);
+
 /* ---- learned inlier weights ------------------------------------------------------------------
  * The thesis has no learned component. These entry points implement the learned variant of the
  * reweighting step the benchmark describes: an MLP 8 -> 32 -> 32 -> 1 (ReLU, sigmoid) predicts

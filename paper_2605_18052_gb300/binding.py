@@ -25,6 +25,7 @@ EXPORTED = [
     "fm_status_string", "fm_last_error", "fm_mlp_num_params", "fm_mlp_create", "fm_mlp_destroy",
     "fm_mlp_get_params", "fm_mlp_set_params", "fm_mlp_train_step", "fm_mlp_gradient", "fm_mlp_forward",
     "fm_set_scores", "fm_collect_features", "fm_learned_weights", "fm_reset_history",
+    "fm_preaggregate", "fm_irls_preaggregate", "fm_loss_grad_quadratic", "fm_step_quadratic",
 ]
 
 
@@ -100,6 +101,10 @@ def load_library(path: str = LIB_PATH):
         "fm_collect_features": (I32, [P, D, I32, P]),
         "fm_learned_weights": (I32, [P, P, D, D, I32, P]),
         "fm_reset_history": (I32, [P]),
+        "fm_preaggregate": (I32, [P]),
+        "fm_irls_preaggregate": (I32, [P, D, P]),
+        "fm_loss_grad_quadratic": (I32, [P, P, P]),
+        "fm_step_quadratic": (I32, [P, I32]),
         "fm_status_string": (ctypes.c_char_p, [I32]),
         "fm_last_error": (ctypes.c_char_p, []),
     }
@@ -332,6 +337,26 @@ class Problem:
 
     def step(self, n_iters: int = 1):
         _check(load_library().fm_step(self._h, int(n_iters)))
+
+    # pre-aggregated quadratic form of the IRLS objective (fixed weights)
+    def preaggregate(self):
+        """Collect the per-image-pair quadratic form at the current poses and weights."""
+        _check(load_library().fm_preaggregate(self._h))
+
+    def irls_preaggregate(self, tau: float) -> int:
+        """IRLS reweighting at threshold tau and the quadratic form, in one pass."""
+        n = ctypes.c_int64()
+        _check(load_library().fm_irls_preaggregate(self._h, float(tau), ctypes.byref(n)))
+        return n.value
+
+    def loss_grad_quadratic(self):
+        loss = ctypes.c_double()
+        g = np.empty((self.n_cams, 6))
+        _check(load_library().fm_loss_grad_quadratic(self._h, ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def step_quadratic(self, n_iters: int = 1):
+        _check(load_library().fm_step_quadratic(self._h, int(n_iters)))
 
     def last_loss(self) -> float:
         loss = ctypes.c_double()

@@ -46,6 +46,9 @@ struct fm_problem {
     cudaGraphExec_t graph8 = nullptr;     // eight chained iterations
     bool timing = false;
     int hist_valid = 0;                   // d.le_hist holds a previous reweighting's residuals
+    bool quad_alloc = false;              // d.qslots, d.quad, d.pair_rec allocated
+    bool quad_valid = false;              // d.quad holds the form of the current weights
+    cudaGraphExec_t qgraph = nullptr, qgraph8 = nullptr;  // quadratic-path iterations
     std::vector<cudaEvent_t> tev;   // timing events, pairs (start, end)
     size_t tev_used = 0;
     int input_was_sorted = 0;
@@ -174,17 +177,25 @@ void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed, bool first) {
     }
 }
 
-// `iters` chained iterations and the closing finalize launch
-void enqueue_iterations(fm_problem *p, cudaStream_t s, bool timed, int iters) {
-    for (int it = 0; it < iters; ++it) enqueue_iteration(p, s, timed, it == 0);
-    launch_finalize(p->d, true, s, !timed);
+// `iters` chained iterations and the closing finalize launch; `quad`: the gradient comes from
+// the pre-aggregated quadratic form (two launches per iteration)
+void enqueue_iterations(fm_problem *p, cudaStream_t s, bool timed, int iters, bool quad = false) {
+    for (int it = 0; it < iters; ++it) {
+        if (quad) {
+            launch_quad_pair(p->d, s, true, it != 0);
+            launch_camera_step(p->d, true, s, true, true);
+        } else {
+            enqueue_iteration(p, s, timed, it == 0);
+        }
+    }
+    launch_finalize(p->d, true, s, quad || !timed);
 }
 
 // a graph of `iters` chained iterations
-fm_status build_graph(fm_problem *p, int iters, cudaGraphExec_t *out) {
+fm_status build_graph(fm_problem *p, int iters, cudaGraphExec_t *out, bool quad = false) {
     cudaGraph_t g = nullptr;
     FM_CUDA(cudaStreamBeginCapture(p->s, cudaStreamCaptureModeThreadLocal));
-    enqueue_iterations(p, p->s, false, iters);
+    enqueue_iterations(p, p->s, false, iters, quad);
     cudaError_t e = cudaStreamEndCapture(p->s, &g);
     if (e != cudaSuccess) return fail(FM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(out, g, 0);
@@ -202,6 +213,8 @@ void free_problem(fm_problem *p) {
     for (void *a : p->allocs) cudaFree(a);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->graph8) cudaGraphExecDestroy(p->graph8);
+    if (p->qgraph) cudaGraphExecDestroy(p->qgraph);
+    if (p->qgraph8) cudaGraphExecDestroy(p->qgraph8);
     for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
@@ -547,6 +560,7 @@ FM_API fm_status fm_set_weights(fm_problem *p, const float *w, int32_t on_device
         src = tmp;
     }
     launch_set_weights(p->d, src, p->s);
+    p->quad_valid = false;
     FM_CUDA(cudaGetLastError());
     if (tmp) FM_CUDA(cudaFreeAsync(tmp, p->s));
     unsigned err = 0;
@@ -642,6 +656,7 @@ FM_API fm_status fm_learned_weights(fm_problem *p, const fm_mlp *net, double tau
     launch_pair_stats(p->d, (float)tau, p->s);
     launch_learned_weights(p->d, master, wbf, (float)tau, std::isinf(tau_cap) ? INFINITY : (float)tau_cap, round,
                            p->hist_valid, p->s);
+    p->quad_valid = false;
     FM_CUDA(cudaGetLastError());
     p->hist_valid = 1;
     unsigned long long cnt = 0;
@@ -660,6 +675,7 @@ FM_API fm_status fm_irls_weights(fm_problem *p, double tau, int64_t *n_active) {
     launch_pair_setup(p->d, p->s);
     const float tf = std::isinf(tau) ? INFINITY : (float)tau;
     launch_irls_weights(p->d, tf, p->s);
+    p->quad_valid = false;
     FM_CUDA(cudaGetLastError());
     unsigned long long cnt = 0;
     FM_CUDA(cudaMemcpyAsync(&cnt, p->d.counter, sizeof cnt, cudaMemcpyDeviceToHost, p->s));
@@ -823,6 +839,100 @@ FM_API fm_status fm_set_state(fm_problem *p, const double *m, const double *v, i
     FM_CUDA(cudaMemcpyAsync(p->d.v, vf.data(), sizeof(float) * n6, cudaMemcpyHostToDevice, p->s));
     FM_CUDA(cudaMemcpyAsync(p->d.step, &s, sizeof s, cudaMemcpyHostToDevice, p->s));
     FM_CUDA(cudaStreamSynchronize(p->s));
+    return FM_OK;
+}
+
+// ---- pre-aggregated quadratic form ------------------------------------------------------------
+namespace {
+
+fm_status quad_prepare(fm_problem *p) {
+    if (p->d.loss != FM_LOSS_IRLS) return fail(FM_EINVAL, "the quadratic form needs the IRLS objective");
+    if (p->quad_alloc) return FM_OK;
+    FM_CUDA(dalloc(p, &p->d.qslots, (size_t)QSLOT * ((size_t)p->d.n_pairs + p->d.n_ranges)));
+    FM_CUDA(dalloc(p, &p->d.quad, (size_t)QREC * p->d.n_pairs));
+    FM_CUDA(dalloc(p, &p->d.pair_rec, (size_t)SLOT * p->d.n_pairs));
+    FM_CUDA(cudaMemsetAsync(p->d.pair_rec, 0, sizeof(float) * SLOT * (size_t)p->d.n_pairs, p->s));
+    p->quad_alloc = true;
+    return FM_OK;
+}
+
+fm_status quad_check(fm_problem *p) {
+    if (p->d.loss != FM_LOSS_IRLS) return fail(FM_EINVAL, "the quadratic form needs the IRLS objective");
+    if (!p->quad_valid)
+        return fail(FM_EINVAL, "no quadratic form for the current weights (call fm_preaggregate first)");
+    return FM_OK;
+}
+
+}  // namespace
+
+FM_API fm_status fm_preaggregate(fm_problem *p) {
+    if (fm_status st = check_problem(p)) return st;
+    FM_CUDA(join_in(p));
+    if (fm_status st = quad_prepare(p)) return st;
+    launch_pair_setup(p->d, p->s);
+    launch_quad_accumulate(p->d, -1.f, p->s);
+    FM_CUDA(cudaGetLastError());
+    p->quad_valid = true;
+    FM_CUDA(join_out(p));
+    return FM_OK;
+}
+
+FM_API fm_status fm_irls_preaggregate(fm_problem *p, double tau, int64_t *n_active) {
+    if (fm_status st = check_problem(p)) return st;
+    if (std::isnan(tau) || tau < 0.0) return fail(FM_EINVAL, "tau must be >= 0 (may be +inf)");
+    FM_CUDA(join_in(p));
+    if (fm_status st = quad_prepare(p)) return st;
+    FM_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(unsigned long long), p->s));
+    launch_pair_setup(p->d, p->s);
+    launch_quad_accumulate(p->d, std::isinf(tau) ? INFINITY : (float)tau, p->s);
+    FM_CUDA(cudaGetLastError());
+    p->quad_valid = true;
+    unsigned long long cnt = 0;
+    FM_CUDA(cudaMemcpyAsync(&cnt, p->d.counter, sizeof cnt, cudaMemcpyDeviceToHost, p->s));
+    if (fm_status st = check_device_errors(p)) return st;
+    if (n_active) *n_active = (int64_t)cnt;
+    FM_CUDA(join_out(p));
+    return FM_OK;
+}
+
+FM_API fm_status fm_loss_grad_quadratic(fm_problem *p, double *loss, double *grad) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!loss) return fail(FM_EINVAL, "loss must not be NULL");
+    if (fm_status st = quad_check(p)) return st;
+    FM_CUDA(join_in(p));
+    launch_quad_pair(p->d, p->s, false, false);
+    launch_camera_step(p->d, false, p->s, false, true);
+    launch_finalize(p->d, false, p->s);
+    FM_CUDA(cudaGetLastError());
+    FM_CUDA(cudaMemcpyAsync(loss, p->d.loss_out, sizeof(double), cudaMemcpyDeviceToHost, p->s));
+    if (grad)
+        FM_CUDA(cudaMemcpyAsync(grad, p->d.grad, sizeof(double) * 6 * p->d.n_cams, cudaMemcpyDeviceToHost, p->s));
+    return check_device_errors(p);
+}
+
+FM_API fm_status fm_step_quadratic(fm_problem *p, int32_t n_iters) {
+    if (fm_status st = check_problem(p)) return st;
+    if (n_iters < 0) return fail(FM_EINVAL, "n_iters must be >= 0");
+    if (fm_status st = quad_check(p)) return st;
+    if (n_iters == 0) return FM_OK;
+    FM_CUDA(join_in(p));
+    if (!p->opt.use_graph) {
+        enqueue_iterations(p, p->s, false, n_iters, true);
+        FM_CUDA(cudaGetLastError());
+    } else {
+        if (!p->qgraph) {
+            fm_status st = build_graph(p, 1, &p->qgraph, true);
+            if (st != FM_OK) return st;
+        }
+        if (n_iters >= 8 && !p->qgraph8) {
+            fm_status st = build_graph(p, 8, &p->qgraph8, true);
+            if (st != FM_OK) return st;
+        }
+        int left = n_iters;
+        for (; left >= 8; left -= 8) FM_CUDA(cudaGraphLaunch(p->qgraph8, p->s));
+        for (; left > 0; --left) FM_CUDA(cudaGraphLaunch(p->qgraph, p->s));
+    }
+    FM_CUDA(join_out(p));
     return FM_OK;
 }
 

@@ -80,7 +80,18 @@ struct DevProblem {
     __half *score;          // per point pair: matcher confidence (0.5 until set)
     __half *le_hist;        // per point pair: log(|eps| + 1e-6) at the previous reweighting
     float *pstat;           // per pair: mean log residual, inlier fraction, log(count)/10, 0
+    // pre-aggregated quadratic form (Eq. epipolar-objective-l2), anchored at the reweighting
+    // point: per (pair, range) partials and per pair records
+    float *qslots;          // (n_pairs + n_ranges) x QSLOT
+    float *quad;            // QREC x n_pairs (component-major): c0, g0(9), M(36), e0(9)
+    float *pair_rec;        // n_pairs x SLOT: per-iteration sums of the quadratic path
 };
+
+// c0 = sum w eps0^2, g0 = sum w eps0 a (9), M = the 36 distinct entries of W = sum w a a^T
+// (a = vec(o2 o1^T); W = (o2 o2^T) (x) (o1 o1^T) summed), e0 = vec(E'_n) at the anchor
+constexpr int QSUMS = 46;
+constexpr int QSLOT = 48;
+constexpr int QREC = 55;
 
 // ---- learned inlier-weight MLP (fm_mlp.cu) ------------------------------------------------------
 constexpr int MLP_IN = 8;
@@ -93,6 +104,10 @@ constexpr int MLP_OFF_W3 = MLP_OFF_B2 + MLP_H;               // W3[k], 32
 constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_H;               // 1
 constexpr int MLP_NPARAM = MLP_OFF_B3 + 1;                   // 1377
 constexpr float LOG_FLOOR = 1e-6f;
+
+// quadratic form: accumulate at the current poses and weights; per-iteration evaluation
+void launch_quad_accumulate(const DevProblem &d, float tau, cudaStream_t s);
+void launch_quad_pair(const DevProblem &d, cudaStream_t s, bool pdl, bool after_step);
 
 // pair statistics of the current residuals (pstat), then features -> MLP -> weights, or the
 // features themselves (input order) for training
@@ -120,7 +135,10 @@ void launch_gather(const DevProblem &d, bool count_step, cudaStream_t s);
 // Adam step of every camera with the gradient in d.grad (FP64, n_cams x 6); advances the step
 void launch_apply_gradient(const DevProblem &d, cudaStream_t s);
 // apply = false computes the gradient and loss only (no Adam step, no step count)
-void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl = false);
+// per_pair: read one record per image pair from d.pair_rec (quadratic path) instead of the
+// streaming pass's per-range partials
+void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl = false,
+                        bool per_pair = false);
 void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s);
 void launch_residuals(const DevProblem &d, float *out_sorted, cudaStream_t s);
 

@@ -186,19 +186,6 @@ __global__ void k_cam_prep(DevProblem d) {
     write_camrec(d.cam + (size_t)k * CAMREC, d.R + 9 * (size_t)k, d.c + 3 * (size_t)k);
 }
 
-// ---- per pair: relative pose and folded essential matrix ------------------------------------------
-__device__ __forceinline__ void load_camrec(const float *rec, float *R, float *hi, float *lo) {
-    const float4 *v = reinterpret_cast<const float4 *>(rec);
-    const float4 a = v[0], b = v[1], c = v[2], e = v[3];
-    R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w;
-    R[4] = b.x; R[5] = b.y; R[6] = b.z; R[7] = b.w;
-    R[8] = c.x;
-    hi[0] = c.y; hi[1] = c.z; hi[2] = c.w;
-    lo[0] = e.x; lo[1] = e.y; lo[2] = e.z;
-}
-
-__device__ __forceinline__ void finish_step(const DevProblem &d, int n_blocks, int count_step);
-
 // prev_blocks > 0: this pass follows an optimiser step whose camera-step kernel had that many
 // blocks; block 0 (with 256 threads) finishes that step's loss total and step count.
 __global__ void __launch_bounds__(256) k_pair_setup(DevProblem d, int prev_blocks) {
@@ -208,72 +195,7 @@ __global__ void __launch_bounds__(256) k_pair_setup(DevProblem d, int prev_block
     pdl_trigger();
     if (prev_blocks > 0 && blockIdx.x == 0) finish_step(d, prev_blocks, 1);
     if (n >= d.n_pairs) return;
-    float Ri[9], Rj[9], hi_i[3], lo_i[3], hi_j[3], lo_j[3], dc[3];
-    load_camrec(d.cam + (size_t)i * CAMREC, Ri, hi_i, lo_i);
-    load_camrec(d.cam + (size_t)j * CAMREC, Rj, hi_j, lo_j);
-    // c_i - c_j from the two-float representation: the high parts of nearby centres
-    // subtract exactly, so the baseline keeps FP32 relative accuracy far from the origin
-#pragma unroll
-    for (int q = 0; q < 3; ++q) dc[q] = (hi_i[q] - hi_j[q]) + (lo_i[q] - lo_j[q]);
-    float Rn[9], tn[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-            Rn[3 * a + b] = Rj[3 * a] * Ri[3 * b] + Rj[3 * a + 1] * Ri[3 * b + 1] + Rj[3 * a + 2] * Ri[3 * b + 2];
-        tn[a] = Rj[3 * a] * dc[0] + Rj[3 * a + 1] * dc[1] + Rj[3 * a + 2] * dc[2];
-    }
-    const float nt2 = tn[0] * tn[0] + tn[1] * tn[1] + tn[2] * tn[2];
-    // a baseline below 1e-10 of the centres' magnitude is rounding noise: its direction,
-    // and so E_n, is undefined
-    float cmax = 1.f;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) cmax = fmaxf(cmax, fmaxf(fabsf(hi_i[q]), fabsf(hi_j[q])));
-    const float floor2 = 1e-20f * cmax * cmax;
-    float inv = 0.f;
-    if (nt2 > floor2 && isfinite(nt2)) {
-        inv = 1.0f / sqrtf(nt2);
-    } else {
-        atomicOr(d.err, ERR_DEGENERATE);
-    }
-    const float th[3] = {tn[0] * inv, tn[1] * inv, tn[2] * inv};
-    // E = [th]_x R_n
-    float E[9];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        E[b] = -th[2] * Rn[3 + b] + th[1] * Rn[6 + b];
-        E[3 + b] = th[2] * Rn[b] - th[0] * Rn[6 + b];
-        E[6 + b] = -th[1] * Rn[b] + th[0] * Rn[3 + b];
-    }
-    // E' = T_j^T E T_i with T = [[1,0,cx],[0,1,cy],[0,0,1]] (keypoints stored as offsets o = x - c)
-    const float2 cen_i = d.cen[i], cen_j = d.cen[j];
-    float g[GEO];
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        g[3 * a] = E[3 * a];
-        g[3 * a + 1] = E[3 * a + 1];
-        g[3 * a + 2] = E[3 * a] * cen_i.x + E[3 * a + 1] * cen_i.y + E[3 * a + 2];
-    }
-    const float m20 = E[6], m21 = E[7], m22 = E[6] * cen_i.x + E[7] * cen_i.y + E[8];
-    g[6] = cen_j.x * g[0] + cen_j.y * g[3] + m20;
-    g[7] = cen_j.x * g[1] + cen_j.y * g[4] + m21;
-    g[8] = cen_j.x * g[2] + cen_j.y * g[5] + m22;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) g[9 + k] = Rn[k];
-    g[18] = tn[0];
-    g[19] = tn[1];
-    g[20] = tn[2];
-    g[21] = inv;
-    g[22] = cen_i.x;
-    g[23] = cen_i.y;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) g[24 + k] = Rj[k];
-    g[33] = cen_j.x;
-    g[34] = cen_j.y;
-    g[35] = 0.f;
-    float4 *out = reinterpret_cast<float4 *>(d.geo + (size_t)n * GEO);
-#pragma unroll
-    for (int k = 0; k < GEO / 4; ++k) out[k] = make_float4(g[4 * k], g[4 * k + 1], g[4 * k + 2], g[4 * k + 3]);
+    pair_geometry(d, n, i, j);
 }
 
 // ---- per pair: combine partials and chain rule ----------------------------------------------------
@@ -558,7 +480,7 @@ __device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const
 constexpr int STEP_CAMS = 8;
 
 __global__ void __launch_bounds__(STEP_CAMS * 32, 4)
-k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
+k_camera_step(DevProblem d, float gscale, float lscale, int apply, int per_pair) {
     __shared__ float s_hi[7][STEP_CAMS], s_lo[7][STEP_CAMS];
     __shared__ int4 s_item[STEP_CAMS][32];
     __shared__ __align__(16) float s_geo[STEP_CAMS][32][GEO];
@@ -568,7 +490,6 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
     __shared__ double s_loss[STEP_CAMS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = blockIdx.x * STEP_CAMS + warp;
-    const long long t_step = *d.step + 1;
     {
         const int cam0 = blockIdx.x * STEP_CAMS;
         for (int i = threadIdx.x; i < STEP_CAMS * 12; i += STEP_CAMS * 32) {
@@ -591,8 +512,12 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
             const int ent = d.cam_ent[e];
             n = ent >> 1;
             role = ent & 1;
-            r0 = d.pair_off[n] / WR;
-            cnt = (d.pair_off[n + 1] - 1) / WR - r0 + 1;
+            if (per_pair) {
+                cnt = 1;
+            } else {
+                r0 = d.pair_off[n] / WR;
+                cnt = (d.pair_off[n + 1] - 1) / WR - r0 + 1;
+            }
             const float4 *gv = reinterpret_cast<const float4 *>(d.geo + (size_t)n * GEO);
             float4 *dst = reinterpret_cast<float4 *>(s_geo[warp][lane]);
 #pragma unroll
@@ -608,9 +533,14 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
         __syncwarp();
         return __shfl_sync(0xffffffffu, incl, 31);
     };
-    int total = load_chunk(e_begin);
-    pdl_wait();     // partial sums of the streaming pass
+    // the streaming pass's geometry records are two launches old and may be read before the
+    // wait; the quadratic path's come from the launch just before this one
+    int total = per_pair ? 0 : load_chunk(e_begin);
+    pdl_wait();     // partial sums of the streaming pass, or the per-pair records
     pdl_trigger();
+    // the previous step is counted by the launch just before this one on the quadratic path
+    const long long t_step = *d.step + 1;
+    if (per_pair) total = load_chunk(e_begin);
     if (k < d.n_cams) {
         float hi[7], lo[7];
 #pragma unroll
@@ -628,8 +558,9 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
                     else hi_i = mid - 1;
                 }
                 const int4 it = s_item[warp][lo_i];
-                const int slot = it.y + it.w + (t - it.x);
-                const float4 *sl = reinterpret_cast<const float4 *>(d.slots + (size_t)slot * SLOT);
+                const float4 *sl = per_pair
+                    ? reinterpret_cast<const float4 *>(d.pair_rec + (size_t)it.y * SLOT)
+                    : reinterpret_cast<const float4 *>(d.slots + (size_t)(it.y + it.w + (t - it.x)) * SLOT);
                 const float4 sa = sl[0], sb = sl[1], sc = sl[2];
                 const float sum[10] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w, sc.x, sc.y};
                 float contrib[7];
@@ -768,26 +699,6 @@ __global__ void k_apply_gradient(DevProblem d) {
 
 __global__ void k_bump_step(DevProblem d) { *d.step += 1; }
 
-// Loss total of a camera-step launch (FP64, fixed order over its blocks) and, after an
-// optimiser step, the step count. One block.
-constexpr int FIN_THREADS = 256;
-
-__device__ __forceinline__ void finish_step(const DevProblem &d, int n_blocks, int count_step) {
-    __shared__ double red[FIN_THREADS];
-    double s = 0.0;
-    for (int q = threadIdx.x; q < n_blocks; q += FIN_THREADS) s += d.cam_loss[q];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = FIN_THREADS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        *d.loss_out = red[0];
-        if (count_step) *d.step += 1;
-    }
-}
-
 __global__ void __launch_bounds__(FIN_THREADS) k_finalize(DevProblem d, int n_blocks, int count_step) {
     pdl_wait();
     pdl_trigger();
@@ -856,11 +767,11 @@ void launch_apply_gradient(const DevProblem &d, cudaStream_t s) {
     k_bump_step<<<1, 1, 0, s>>>(d);
 }
 
-void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl) {
+void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl, bool per_pair) {
     float gscale, lscale;
     loss_scales(d, gscale, lscale);
     launch_k(k_camera_step, dim3(blocks_for(d.n_cams, STEP_CAMS)), dim3(STEP_CAMS * 32), s, pdl, d,
-             gscale, lscale, apply ? 1 : 0);
+             gscale, lscale, apply ? 1 : 0, per_pair ? 1 : 0);
 }
 
 void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s) {

@@ -197,4 +197,119 @@ __device__ __forceinline__ void walk_range(const DevProblem &d, int r, int lane,
     body.segment_end(seg, r, lane, true);
 }
 
+// ---- per pair: relative pose and folded essential matrix ------------------------------------------
+__device__ __forceinline__ void load_camrec(const float *rec, float *R, float *hi, float *lo) {
+    const float4 *v = reinterpret_cast<const float4 *>(rec);
+    const float4 a = v[0], b = v[1], c = v[2], e = v[3];
+    R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w;
+    R[4] = b.x; R[5] = b.y; R[6] = b.z; R[7] = b.w;
+    R[8] = c.x;
+    hi[0] = c.y; hi[1] = c.z; hi[2] = c.w;
+    lo[0] = e.x; lo[1] = e.y; lo[2] = e.z;
+}
+
+
+// Relative pose and centroid-folded essential matrix of pair n = (i, j), written to its
+// geometry record: E'_n = T_j^T [t_n/|t_n|]_x R_n T_i, R_n = R_j R_i^T, t_n = R_j (c_i - c_j).
+// E_out (optional): receives E'_n as well.
+__device__ __forceinline__ void pair_geometry(const DevProblem &d, int n, int i, int j, float *E_out = nullptr) {
+    float Ri[9], Rj[9], hi_i[3], lo_i[3], hi_j[3], lo_j[3], dc[3];
+    load_camrec(d.cam + (size_t)i * CAMREC, Ri, hi_i, lo_i);
+    load_camrec(d.cam + (size_t)j * CAMREC, Rj, hi_j, lo_j);
+    // c_i - c_j from the two-float representation: the high parts of nearby centres
+    // subtract exactly, so the baseline keeps FP32 relative accuracy far from the origin
+#pragma unroll
+    for (int q = 0; q < 3; ++q) dc[q] = (hi_i[q] - hi_j[q]) + (lo_i[q] - lo_j[q]);
+    float Rn[9], tn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            Rn[3 * a + b] = Rj[3 * a] * Ri[3 * b] + Rj[3 * a + 1] * Ri[3 * b + 1] + Rj[3 * a + 2] * Ri[3 * b + 2];
+        tn[a] = Rj[3 * a] * dc[0] + Rj[3 * a + 1] * dc[1] + Rj[3 * a + 2] * dc[2];
+    }
+    const float nt2 = tn[0] * tn[0] + tn[1] * tn[1] + tn[2] * tn[2];
+    // a baseline below 1e-10 of the centres' magnitude is rounding noise: its direction,
+    // and so E_n, is undefined
+    float cmax = 1.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cmax = fmaxf(cmax, fmaxf(fabsf(hi_i[q]), fabsf(hi_j[q])));
+    const float floor2 = 1e-20f * cmax * cmax;
+    float inv = 0.f;
+    if (nt2 > floor2 && isfinite(nt2)) {
+        inv = 1.0f / sqrtf(nt2);
+    } else {
+        atomicOr(d.err, ERR_DEGENERATE);
+    }
+    const float th[3] = {tn[0] * inv, tn[1] * inv, tn[2] * inv};
+    // E = [th]_x R_n
+    float E[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        E[b] = -th[2] * Rn[3 + b] + th[1] * Rn[6 + b];
+        E[3 + b] = th[2] * Rn[b] - th[0] * Rn[6 + b];
+        E[6 + b] = -th[1] * Rn[b] + th[0] * Rn[3 + b];
+    }
+    // E' = T_j^T E T_i with T = [[1,0,cx],[0,1,cy],[0,0,1]] (keypoints stored as offsets o = x - c)
+    const float2 cen_i = d.cen[i], cen_j = d.cen[j];
+    float g[GEO];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        g[3 * a] = E[3 * a];
+        g[3 * a + 1] = E[3 * a + 1];
+        g[3 * a + 2] = E[3 * a] * cen_i.x + E[3 * a + 1] * cen_i.y + E[3 * a + 2];
+    }
+    const float m20 = E[6], m21 = E[7], m22 = E[6] * cen_i.x + E[7] * cen_i.y + E[8];
+    g[6] = cen_j.x * g[0] + cen_j.y * g[3] + m20;
+    g[7] = cen_j.x * g[1] + cen_j.y * g[4] + m21;
+    g[8] = cen_j.x * g[2] + cen_j.y * g[5] + m22;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[9 + k] = Rn[k];
+    g[18] = tn[0];
+    g[19] = tn[1];
+    g[20] = tn[2];
+    g[21] = inv;
+    g[22] = cen_i.x;
+    g[23] = cen_i.y;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[24 + k] = Rj[k];
+    g[33] = cen_j.x;
+    g[34] = cen_j.y;
+    g[35] = 0.f;
+    if (E_out) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) E_out[k] = g[k];
+    }
+    float4 *out = reinterpret_cast<float4 *>(d.geo + (size_t)n * GEO);
+#pragma unroll
+    for (int k = 0; k < GEO / 4; ++k) out[k] = make_float4(g[4 * k], g[4 * k + 1], g[4 * k + 2], g[4 * k + 3]);
+}
+
+// Loss total of a camera-step launch (FP64, fixed order over its blocks) and, after an
+// optimiser step, the step count. One block of NT threads (NT divides FIN_THREADS); the
+// summation order is that of FIN_THREADS threads whatever NT is, so every launch that
+// finishes a step produces the same bits.
+constexpr int FIN_THREADS = 256;
+
+template <int NT = FIN_THREADS>
+__device__ __forceinline__ void finish_step(const DevProblem &d, int n_blocks, int count_step) {
+    static_assert(FIN_THREADS % NT == 0, "block must divide FIN_THREADS");
+    __shared__ double red[FIN_THREADS];
+#pragma unroll
+    for (int v = threadIdx.x; v < FIN_THREADS; v += NT) {
+        double s = 0.0;
+        for (int q = v; q < n_blocks; q += FIN_THREADS) s += d.cam_loss[q];
+        red[v] = s;
+    }
+    __syncthreads();
+    for (int w = FIN_THREADS / 2; w > 0; w >>= 1) {
+        for (int v = threadIdx.x; v < w; v += NT) red[v] += red[v + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *d.loss_out = red[0];
+        if (count_step) *d.step += 1;
+    }
+}
+
 }  // namespace fm

@@ -65,8 +65,10 @@ def train(net: Mlp, X: torch.Tensor, Y: torch.Tensor, steps: int, batch: int, lr
     return losses
 
 
-def refine_learned(problem, net: Mlp, schedule: Schedule, callback=None, first_round: int = 0):
-    """The IRLS loop with learned reweighting: w = p / max(|eps|, delta) for |eps| <= tau_r."""
+def refine_learned(problem, net: Mlp, schedule: Schedule, callback=None, first_round: int = 0,
+                   quadratic: bool = False):
+    """The IRLS loop with learned reweighting: w = p / max(|eps|, delta) for |eps| <= tau_r.
+    quadratic: iterate on the pre-aggregated quadratic form of each round's objective."""
     if first_round == 0:
         problem.reset_history()
     for r in range(first_round, schedule.rounds):
@@ -74,7 +76,11 @@ def refine_learned(problem, net: Mlp, schedule: Schedule, callback=None, first_r
         problem.learned_weights(net, tau, tau, r)
         s = schedule.decay ** r
         problem.set_learning_rate(schedule.lr_rot * s, schedule.lr_c * s)
-        problem.step(schedule.iters_per_round)
+        if quadratic:
+            problem.preaggregate()
+            problem.step_quadratic(schedule.iters_per_round)
+        else:
+            problem.step(schedule.iters_per_round)
         if callback is not None:
             callback(r, problem)
     return problem
@@ -128,7 +134,8 @@ def time_to_accuracy(sc, arm: str, net: Mlp | None = None, storage: str = "fp16"
     """Device time of the refinement loop until the mean rotation error (after global
     alignment) is <= threshold_deg, and the time at which each of `thresholds` was first
     reached. The error is checked after every round and the check is not timed.
-    arm: "irls" (plain reweighting) or "learned". Returns a dict."""
+    arm: "irls" (plain reweighting) or "learned", each optionally with the suffix "_quad"
+    (iterations on the pre-aggregated quadratic form). Returns a dict."""
     from . import metrics
     from .binding import Problem, default_options
     sch = default_schedule(sc, max_rounds)
@@ -145,13 +152,23 @@ def time_to_accuracy(sc, arm: str, net: Mlp | None = None, storage: str = "fp16"
             torch.cuda.synchronize()
             e0.record(stream)
             tau = sch.tau(r)
-            if arm == "irls":
-                gp.irls_weights(tau)
-            else:
-                gp.learned_weights(net, tau, tau, r)
             s = sch.decay ** r
             gp.set_learning_rate(sch.lr_rot * s, sch.lr_c * s)
-            gp.step(sch.iters_per_round)
+            if arm == "irls":
+                gp.irls_weights(tau)
+                gp.step(sch.iters_per_round)
+            elif arm == "irls_quad":
+                gp.irls_preaggregate(tau)
+                gp.step_quadratic(sch.iters_per_round)
+            elif arm == "learned":
+                gp.learned_weights(net, tau, tau, r)
+                gp.step(sch.iters_per_round)
+            elif arm == "learned_quad":
+                gp.learned_weights(net, tau, tau, r)
+                gp.preaggregate()
+                gp.step_quadratic(sch.iters_per_round)
+            else:
+                raise ValueError(f"unknown arm {arm!r}")
             e1.record(stream)
             torch.cuda.synchronize()
             total_ms += e0.elapsed_time(e1)

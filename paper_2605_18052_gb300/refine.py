@@ -4,6 +4,12 @@ Each round reweights the point pairs at the current poses with a filtering thres
 starts large and shrinks by a constant factor every round down to a floor, then runs a fixed
 number of Adam iterations on the reweighted objective. All per-point-pair work happens inside the library
 calls (fm_irls_weights, fm_step).
+
+With `quadratic=True` a round makes one pass over the point pairs (reweighting and the
+per-image-pair quadratic form of the reweighted objective, fm_irls_preaggregate) and its
+iterations evaluate the objective from the form alone (fm_step_quadratic). With the weights
+fixed the objective is exactly quadratic in each essential matrix, so both modes follow the
+same trajectory up to FP32 rounding.
 """
 from __future__ import annotations
 
@@ -25,13 +31,17 @@ class Schedule:
         return max(self.tau_min, self.tau0 * self.tau_factor ** r)
 
 
-def refine(problem, schedule: Schedule, callback=None, first_round: int = 0):
+def refine(problem, schedule: Schedule, callback=None, first_round: int = 0, quadratic: bool = False):
     """Run `schedule` on `problem` (a binding.Problem). callback(r, problem) after each round."""
     for r in range(first_round, schedule.rounds):
-        problem.irls_weights(schedule.tau(r))
         s = schedule.decay ** r
         problem.set_learning_rate(schedule.lr_rot * s, schedule.lr_c * s)
-        problem.step(schedule.iters_per_round)
+        if quadratic:
+            problem.irls_preaggregate(schedule.tau(r))
+            problem.step_quadratic(schedule.iters_per_round)
+        else:
+            problem.irls_weights(schedule.tau(r))
+            problem.step(schedule.iters_per_round)
         if callback is not None:
             callback(r, problem)
     return problem
