@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-tta", action="store_true", help="skip the time-to-accuracy comparison")
+    ap.add_argument("--no-quad", action="store_true", help="skip the quadratic-form timing")
     ap.add_argument("--tta-config", default="traj1000_o30")
     ap.add_argument("--tta-rounds", type=int, default=120)
     return ap.parse_args()
@@ -58,15 +59,30 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# the sources a kernel's code comes from; a committed traffic figure is used only while their
+# combined hash matches the one recorded with it
+KERNEL_SOURCES = {
+    "stream_loss": ("fm_kernels.cu", "fm_walk.cuh", "fm_internal.cuh"),
+    "quad_accumulate": ("fm_quad.cu", "fm_walk.cuh", "fm_internal.cuh"),
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2605_18052_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(kernel_tag: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
-    kernel source (the summary records the source hash); else None."""
-    import hashlib
-    src = os.path.join(ROOT, "paper_2605_18052_gb300", "csrc", "fm_kernels.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    kernel sources (the summary records their hash); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
+    h = kernel_source_hash(kernel_tag.split("_fp")[0])
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel_tag and parts[1] == h:
@@ -243,7 +259,7 @@ def main():
     sc = scenegen.make_scene(args.config, seed=args.seed + rank, device="cuda")
     torch.cuda.empty_cache()   # drop the generator's temporaries
     sch = schedule_for(sc, args.iters)
-    opt = fm.default_options(storage=args.storage, lr_rot=sch.lr_rot, lr_c=sch.lr_c)
+    opt = sch.options(storage=args.storage)
     stream = torch.cuda.current_stream()
     gp = fm.Problem(sc.R_init.cpu(), sc.t_init.cpu(), sc.cam_i.cpu(), sc.cam_j.cpu(), sc.pair_id,
                     sc.x1, sc.x2, options=opt)
@@ -299,8 +315,41 @@ def main():
                 "kernel": f"k_stream_loss<{args.storage.upper()}, IRLS>",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs burst copy)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6}
-    launches = args.steps * (2 + 3 * args.iters)
+    # per step: reweighting (pair setup + weights), 3 launches per iteration, and one finalize per
+    # graph launch (graphs of 8 chained iterations, then single iterations)
+    launches = args.steps * (2 + 3 * args.iters + args.iters // 8 + args.iters % 8)
     clocks = clk.summary()
+
+    # the same rounds on the pre-aggregated quadratic form: one pass over the point pairs per
+    # round (reweighting fused with the form), iterations in O(image pairs)
+    quad = None
+    if not args.no_quad:
+        def quad_round(r):
+            gp.irls_preaggregate(sch.tau(r % sch.rounds))
+            gp.step_quadratic(args.iters)
+        for r in range(args.warmup):
+            quad_round(r)
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q2 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for k in range(args.steps):
+            quad_round(args.warmup + k)
+        q1.record(stream)
+        for k in range(args.steps):
+            gp.step_quadratic(args.iters)
+        q2.record(stream)
+        torch.cuda.synchronize()
+        q_ms = q0.elapsed_time(q1) / args.steps
+        it_us = q1.elapsed_time(q2) / args.steps / args.iters * 1e3
+        quad = {"ms_per_step": q_ms, "iteration_us": it_us,
+                "reweight_and_form_ms": q_ms - it_us * args.iters * 1e-3,
+                "equivalent_value": float(n_pp) * args.iters / (q_ms * 1e-3) / 1e9, "unit": UNIT,
+                "form_pass_traffic": profiled_traffic(f"quad_accumulate_{args.storage}_{args.config}"),
+                "note": "same step (1 reweighting round + iters iterations) with the gradient taken from the "
+                        "per-image-pair quadratic form; equivalent_value counts the point pairs the "
+                        "streaming path would have read"}
 
     # end to end through the public API with pinned host buffers: create + full schedule + poses
     e2e = None
@@ -352,7 +401,7 @@ def main():
                           "l2": "inputs larger than L2 (no flush needed)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "time_to_accuracy": tta,
+               "time_to_accuracy": tta, "quadratic_path": quad,
                "clocks": clocks, "hbm_frac_of_step": value * 1e9 * bytes_per_launch / n_pp / 1e9 / peak}
         print(json.dumps(out))
     if world > 1:

@@ -26,9 +26,18 @@ class Schedule:
     decay: float = 0.95       # learning-rate factor per round
     lr_rot: float = 1e-2      # radians
     lr_c: float = 1e-2        # scene units (scale with the typical baseline)
+    delta: float = 1e-6       # IRLS weight floor: w = 1/max(|eps|, delta) (a problem option)
+    beta2: float = 0.999      # Adam second-moment decay (a problem option)
 
     def tau(self, r: int) -> float:
         return max(self.tau_min, self.tau0 * self.tau_factor ** r)
+
+    def options(self, **kw):
+        """Problem options carrying this schedule's step sizes, weight floor and Adam beta2."""
+        from .binding import default_options
+        base = dict(lr_rot=self.lr_rot, lr_c=self.lr_c, delta=self.delta, beta2=self.beta2)
+        base.update(kw)
+        return default_options(**base)
 
 
 def refine(problem, schedule: Schedule, callback=None, first_round: int = 0, quadratic: bool = False):

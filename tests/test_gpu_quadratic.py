@@ -158,7 +158,7 @@ def test_quadratic_refine_reaches_the_streaming_accuracy():
     sch = learned.default_schedule(sc, rounds=20)
     errs = []
     for quadratic in (False, True):
-        with _gpu_problem(sc, R0, t0, lr_rot=sch.lr_rot, lr_c=sch.lr_c) as gp:
+        with fm.Problem(R0, t0, sc.cam_i, sc.cam_j, sc.pair_id, sc.x1, sc.x2, options=sch.options()) as gp:
             fm.refine(gp, sch, quadratic=quadratic)
             R, _ = gp.get_poses()
         errs.append(O.rotation_error_deg(R, Rg).mean())
