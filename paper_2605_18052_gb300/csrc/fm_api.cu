@@ -177,18 +177,21 @@ void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed, bool first) {
     }
 }
 
-// `iters` chained iterations and the closing finalize launch; `quad`: the gradient comes from
-// the pre-aggregated quadratic form (two launches per iteration)
+// `iters` chained iterations and the closing finalize launch; `quad`: fused steps on the
+// pre-aggregated quadratic form (one launch per iteration), alternating between the two
+// camera-record buffers; after an odd count the finalize launch copies the records back
 void enqueue_iterations(fm_problem *p, cudaStream_t s, bool timed, int iters, bool quad = false) {
-    for (int it = 0; it < iters; ++it) {
-        if (quad) {
-            launch_quad_pair(p->d, s, true, it != 0);
-            launch_camera_step(p->d, true, s, true, true);
-        } else {
-            enqueue_iteration(p, s, timed, it == 0);
+    if (quad) {
+        for (int it = 0; it < iters; ++it) {
+            const bool even = (it & 1) == 0;
+            launch_quad_step(p->d, it, even ? p->d.cam : p->d.cam_alt, even ? p->d.cam_alt : p->d.cam, true, s,
+                             true);
         }
+        launch_finalize_n(p->d, iters, (iters & 1) ? p->d.cam_alt : nullptr, s, true);
+        return;
     }
-    launch_finalize(p->d, true, s, quad || !timed);
+    for (int it = 0; it < iters; ++it) enqueue_iteration(p, s, timed, it == 0);
+    launch_finalize(p->d, true, s, !timed);
 }
 
 // a graph of `iters` chained iterations
@@ -850,8 +853,7 @@ fm_status quad_prepare(fm_problem *p) {
     if (p->quad_alloc) return FM_OK;
     FM_CUDA(dalloc(p, &p->d.qslots, (size_t)QSLOT * ((size_t)p->d.n_pairs + p->d.n_ranges)));
     FM_CUDA(dalloc(p, &p->d.quad, (size_t)QREC * p->d.n_pairs));
-    FM_CUDA(dalloc(p, &p->d.pair_rec, (size_t)SLOT * p->d.n_pairs));
-    FM_CUDA(cudaMemsetAsync(p->d.pair_rec, 0, sizeof(float) * SLOT * (size_t)p->d.n_pairs, p->s));
+    FM_CUDA(dalloc(p, &p->d.cam_alt, (size_t)CAMREC * p->d.n_cams));
     p->quad_alloc = true;
     return FM_OK;
 }
@@ -900,8 +902,7 @@ FM_API fm_status fm_loss_grad_quadratic(fm_problem *p, double *loss, double *gra
     if (!loss) return fail(FM_EINVAL, "loss must not be NULL");
     if (fm_status st = quad_check(p)) return st;
     FM_CUDA(join_in(p));
-    launch_quad_pair(p->d, p->s, false, false);
-    launch_camera_step(p->d, false, p->s, false, true);
+    launch_quad_step(p->d, 0, p->d.cam, p->d.cam_alt, false, p->s, false);
     launch_finalize(p->d, false, p->s);
     FM_CUDA(cudaGetLastError());
     FM_CUDA(cudaMemcpyAsync(loss, p->d.loss_out, sizeof(double), cudaMemcpyDeviceToHost, p->s));

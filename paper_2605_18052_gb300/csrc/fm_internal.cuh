@@ -83,15 +83,15 @@ struct DevProblem {
     // pre-aggregated quadratic form (Eq. epipolar-objective-l2), anchored at the reweighting
     // point: per (pair, range) partials and per pair records
     float *qslots;          // (n_pairs + n_ranges) x QSLOT
-    float *quad;            // QREC x n_pairs (component-major): c0, g0(9), M(36), e0(9)
-    float *pair_rec;        // n_pairs x SLOT: per-iteration sums of the quadratic path
+    float *quad;            // n_pairs x QREC: c0, g0(9), M(36), e0(9), pad
+    float *cam_alt;         // n_cams x CAMREC: second camera-record buffer of the fused step
 };
 
 // c0 = sum w eps0^2, g0 = sum w eps0 a (9), M = the 36 distinct entries of W = sum w a a^T
 // (a = vec(o2 o1^T); W = (o2 o2^T) (x) (o1 o1^T) summed), e0 = vec(E'_n) at the anchor
 constexpr int QSUMS = 46;
 constexpr int QSLOT = 48;
-constexpr int QREC = 55;
+constexpr int QREC = 56;
 
 // ---- learned inlier-weight MLP (fm_mlp.cu) ------------------------------------------------------
 constexpr int MLP_IN = 8;
@@ -107,7 +107,10 @@ constexpr float LOG_FLOOR = 1e-6f;
 
 // quadratic form: accumulate at the current poses and weights; per-iteration evaluation
 void launch_quad_accumulate(const DevProblem &d, float tau, cudaStream_t s);
-void launch_quad_pair(const DevProblem &d, cudaStream_t s, bool pdl, bool after_step);
+// one fused step on the form: iteration `it` of a chain (Adam step count *d.step + 1 + it),
+// camera records read from cam_src and written to cam_dst (apply = false: gradient and loss only)
+void launch_quad_step(const DevProblem &d, int it, const float *cam_src, float *cam_dst, bool apply,
+                      cudaStream_t s, bool pdl);
 
 // pair statistics of the current residuals (pstat), then features -> MLP -> weights, or the
 // features themselves (input order) for training
@@ -125,7 +128,12 @@ void launch_cam_prep(const DevProblem &d, cudaStream_t s);
 void launch_pair_setup(const DevProblem &d, cudaStream_t s, bool pdl = false, bool after_step = false);
 // loss total of the last camera step (and the step count after an optimiser step)
 void launch_finalize(const DevProblem &d, bool count_step, cudaStream_t s, bool pdl = false);
+// the same with `count` steps added, and camera records copied back from copy_src if not null
+void launch_finalize_n(const DevProblem &d, int count, const float *copy_src, cudaStream_t s, bool pdl);
 int camera_step_blocks(const DevProblem &d);
+// factors applied to the raw sums of the loss (Sum w eps^2 or Sum |eps|, weights stored as
+// w * s): gradient 2/(Z s) and loss 1/(Z s) for IRLS, 1/Z for L1
+void loss_scales(const DevProblem &d, float &gscale, float &lscale);
 // streaming loss + adjoint: per (image pair, CTA range) partial sums in d.slots
 void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl = false);
 void launch_combine(const DevProblem &d, cudaStream_t s);
@@ -135,10 +143,7 @@ void launch_gather(const DevProblem &d, bool count_step, cudaStream_t s);
 // Adam step of every camera with the gradient in d.grad (FP64, n_cams x 6); advances the step
 void launch_apply_gradient(const DevProblem &d, cudaStream_t s);
 // apply = false computes the gradient and loss only (no Adam step, no step count)
-// per_pair: read one record per image pair from d.pair_rec (quadratic path) instead of the
-// streaming pass's per-range partials
-void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl = false,
-                        bool per_pair = false);
+void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl = false);
 void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s);
 void launch_residuals(const DevProblem &d, float *out_sorted, cudaStream_t s);
 

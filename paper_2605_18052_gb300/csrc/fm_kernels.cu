@@ -11,19 +11,9 @@
 //   irls_weights / residuals: the same streaming walk writing one value per point pair
 #include <math.h>
 
-#include "fm_walk.cuh"
+#include "fm_step.cuh"
 
 namespace fm {
-
-// (hi, lo) += (bhi, blo) with the rounding error of the high parts kept (Knuth's TwoSum)
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float bhi, float blo) {
-    const float s = hi + bhi;
-    const float bb = s - hi;
-    const float err = (hi - (s - bb)) + (bhi - bb);
-    const float l = lo + blo + err;
-    hi = s + l;
-    lo = l - (hi - s);
-}
 
 // ---- loss + adjoint -----------------------------------------------------------------------------
 // acc[0..8] = sum s * o2 o1^T (row-major), acc[9] = sum of loss terms, with s = w*eps (IRLS,
@@ -167,19 +157,6 @@ __global__ void __launch_bounds__(CTA_WARPS * 32) k_residuals(DevProblem d, floa
     walk_range<STORE, false>(d, r, threadIdx.x & 31, body);
 }
 
-// ---- per camera: pose record --------------------------------------------------------------------
-__device__ __forceinline__ void write_camrec(float *rec, const double *R, const double *c) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) rec[i] = (float)R[i];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const float hi = (float)c[q];
-        rec[9 + q] = hi;
-        rec[12 + q] = (float)(c[q] - (double)hi);
-    }
-    rec[15] = 0.f;
-}
-
 __global__ void k_cam_prep(DevProblem d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n_cams) return;
@@ -199,12 +176,6 @@ __global__ void __launch_bounds__(256) k_pair_setup(DevProblem d, int prev_block
 }
 
 // ---- per pair: combine partials and chain rule ----------------------------------------------------
-__device__ __forceinline__ void vee(const float *M, float *v) {
-    v[0] = M[7] - M[5];
-    v[1] = M[2] - M[6];
-    v[2] = M[3] - M[1];
-}
-
 __global__ void k_combine(DevProblem d, float gscale, float lscale) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= d.n_pairs) return;
@@ -333,132 +304,6 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather(DevProblem d, int cou
 }
 
 // ---- per camera: Adam + exponential map (FP64) -----------------------------------------------------
-// Exp(phi) by Rodrigues' formula, R = I + a K + b K^2 with K = [phi]_x. For |phi| < 0.1
-// (every Adam step: |phi| <= lr) a = sin(t)/t and b = (1 - cos(t))/t^2 come from their Taylor
-// series in t^2 through the t^8 terms (truncation < 3e-18, below half an FP64 ulp of 1),
-// which avoids FP64 sin/cos/sqrt/division on GB300's narrow FP64 pipe.
-__device__ void expmap64(const double *phi, double *R) {
-    const double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
-    double a, b;
-    if (th2 < 0.01) {
-        a = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0))));
-        b = 0.5 * (1.0 - th2 * (1.0 / 12.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0) * (1.0 - th2 * (1.0 / 90.0)))));
-    } else {
-        const double th = sqrt(th2);
-        double sn, cs;
-        sincos(th, &sn, &cs);
-        a = sn / th;
-        b = (1.0 - cs) / th2;
-    }
-    const double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double k2 = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
-            R[3 * r + c] = (r == c ? 1.0 : 0.0) + a * K[3 * r + c] + b * k2;
-        }
-}
-
-// 1/sqrt(x) in FP64: an FP32 seed refined by two Newton steps (the relative error squares
-// each step: ~2e-7 -> ~1e-13 -> below FP64 rounding)
-__device__ __forceinline__ double rsqrt64(double x) {
-    double y = (double)rsqrtf((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
-    y = y * (1.5 - 0.5 * x * y * y);
-    return y;
-}
-
-// Gram-Schmidt on the rows: r0 normalised, r1 orthogonalised and normalised, r2 = r0 x r1
-__device__ void orthonormalize_rows(double *R) {
-    const double n0 = rsqrt64(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
-    for (int q = 0; q < 3; ++q) R[q] *= n0;
-    const double dp = R[0] * R[3] + R[1] * R[4] + R[2] * R[5];
-    for (int q = 0; q < 3; ++q) R[3 + q] -= dp * R[q];
-    const double n1 = rsqrt64(R[3] * R[3] + R[4] * R[4] + R[5] * R[5]);
-    for (int q = 0; q < 3; ++q) R[3 + q] *= n1;
-    R[6] = R[1] * R[5] - R[2] * R[4];
-    R[7] = R[2] * R[3] - R[0] * R[5];
-    R[8] = R[0] * R[4] - R[1] * R[3];
-}
-
-// Chain rule of one image pair (or one range partial of it) to one of its cameras.
-// gr = the pair's geometry record, sum[0..8] = sum s * o2 o1^T over the point pairs,
-// sum[9] = their loss terms. Writes the camera's 6 gradient components and (for the first
-// camera only) the loss.
-__device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const float *sum,
-                                                float gscale, float lscale, float *contrib) {
-    float Gp[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) Gp[q] = sum[q] * gscale;
-    const float2 cen_i = make_float2(gr[22], gr[23]), cen_j = make_float2(gr[33], gr[34]);
-    float M[9], G[9];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        M[3 * a] = Gp[3 * a] + Gp[3 * a + 2] * cen_i.x;
-        M[3 * a + 1] = Gp[3 * a + 1] + Gp[3 * a + 2] * cen_i.y;
-        M[3 * a + 2] = Gp[3 * a + 2];
-    }
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        G[b] = M[b] + cen_j.x * M[6 + b];
-        G[3 + b] = M[3 + b] + cen_j.y * M[6 + b];
-        G[6 + b] = M[6 + b];
-    }
-    const float *Rn = gr + 9;
-    const float tn[3] = {gr[18], gr[19], gr[20]};
-    const float inv = gr[21];
-    const float *Rj = gr + 24;
-    const float th[3] = {tn[0] * inv, tn[1] * inv, tn[2] * inv};
-    float A[9];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        A[b] = -(-th[2] * G[3 + b] + th[1] * G[6 + b]);
-        A[3 + b] = -(th[2] * G[b] - th[0] * G[6 + b]);
-        A[6 + b] = -(-th[1] * G[b] + th[0] * G[3 + b]);
-    }
-    float GRt[9];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-            GRt[3 * a + b] = G[3 * a] * Rn[3 * b] + G[3 * a + 1] * Rn[3 * b + 1] + G[3 * a + 2] * Rn[3 * b + 2];
-    float gth[3], gt[3], gc[3], gp[3];
-    vee(GRt, gth);
-    const float dp = th[0] * gth[0] + th[1] * gth[1] + th[2] * gth[2];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) gt[q] = (gth[q] - dp * th[q]) * inv;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) gc[q] = Rj[q] * gt[0] + Rj[3 + q] * gt[1] + Rj[6 + q] * gt[2];
-    if (role == 0) {
-        float RtA[9];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) RtA[3 * a + b] = Rn[a] * A[b] + Rn[3 + a] * A[3 + b] + Rn[6 + a] * A[6 + b];
-        vee(RtA, gp);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            contrib[q] = -gp[q];
-            contrib[3 + q] = gc[q];
-        }
-        contrib[6] = sum[9] * lscale;
-    } else {
-        float ARt[9];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) ARt[3 * a + b] = A[3 * a] * Rn[3 * b] + A[3 * a + 1] * Rn[3 * b + 1] + A[3 * a + 2] * Rn[3 * b + 2];
-        vee(ARt, gp);
-        contrib[0] = gp[0] + (tn[1] * gt[2] - tn[2] * gt[1]);
-        contrib[1] = gp[1] + (tn[2] * gt[0] - tn[0] * gt[2]);
-        contrib[2] = gp[2] + (tn[0] * gt[1] - tn[1] * gt[0]);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) contrib[3 + q] = -gc[q];
-        contrib[6] = 0.f;
-    }
-}
-
 // Fused per-camera step, 8 cameras per 256-thread block (all blocks resident at once).
 // Before waiting for the streaming pass (griddepcontrol.wait) the block fetches everything that
 // is at least two kernels old: its cameras' Adam moments, poses and the step count, and for
@@ -477,10 +322,8 @@ __device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const
 // which another block may be updating. The loss of a pair is counted by its first camera
 // only; each block writes the FP64 sum of its cameras' losses to cam_loss[block], and the
 // next kernel (pair setup or the finalize kernel) adds them up and advances the step count.
-constexpr int STEP_CAMS = 8;
-
 __global__ void __launch_bounds__(STEP_CAMS * 32, 4)
-k_camera_step(DevProblem d, float gscale, float lscale, int apply, int per_pair) {
+k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
     __shared__ float s_hi[7][STEP_CAMS], s_lo[7][STEP_CAMS];
     __shared__ int4 s_item[STEP_CAMS][32];
     __shared__ __align__(16) float s_geo[STEP_CAMS][32][GEO];
@@ -512,12 +355,8 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply, int per_pair)
             const int ent = d.cam_ent[e];
             n = ent >> 1;
             role = ent & 1;
-            if (per_pair) {
-                cnt = 1;
-            } else {
-                r0 = d.pair_off[n] / WR;
-                cnt = (d.pair_off[n + 1] - 1) / WR - r0 + 1;
-            }
+            r0 = d.pair_off[n] / WR;
+            cnt = (d.pair_off[n + 1] - 1) / WR - r0 + 1;
             const float4 *gv = reinterpret_cast<const float4 *>(d.geo + (size_t)n * GEO);
             float4 *dst = reinterpret_cast<float4 *>(s_geo[warp][lane]);
 #pragma unroll
@@ -533,14 +372,10 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply, int per_pair)
         __syncwarp();
         return __shfl_sync(0xffffffffu, incl, 31);
     };
-    // the streaming pass's geometry records are two launches old and may be read before the
-    // wait; the quadratic path's come from the launch just before this one
-    int total = per_pair ? 0 : load_chunk(e_begin);
-    pdl_wait();     // partial sums of the streaming pass, or the per-pair records
+    int total = load_chunk(e_begin);
+    pdl_wait();     // partial sums of the streaming pass
     pdl_trigger();
-    // the previous step is counted by the launch just before this one on the quadratic path
     const long long t_step = *d.step + 1;
-    if (per_pair) total = load_chunk(e_begin);
     if (k < d.n_cams) {
         float hi[7], lo[7];
 #pragma unroll
@@ -558,9 +393,7 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply, int per_pair)
                     else hi_i = mid - 1;
                 }
                 const int4 it = s_item[warp][lo_i];
-                const float4 *sl = per_pair
-                    ? reinterpret_cast<const float4 *>(d.pair_rec + (size_t)it.y * SLOT)
-                    : reinterpret_cast<const float4 *>(d.slots + (size_t)(it.y + it.w + (t - it.x)) * SLOT);
+                const float4 *sl = reinterpret_cast<const float4 *>(d.slots + (size_t)(it.y + it.w + (t - it.x)) * SLOT);
                 const float4 sa = sl[0], sb = sl[1], sc = sl[2];
                 const float sum[10] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w, sc.x, sc.y};
                 float contrib[7];
@@ -569,14 +402,7 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply, int per_pair)
                 for (int q = 0; q < 7; ++q) two_sum_acc(hi[q], lo[q], contrib[q], 0.f);
             }
         }
-#pragma unroll
-        for (int q = 0; q < 7; ++q)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float bh = __shfl_xor_sync(0xffffffffu, hi[q], o);
-                const float bl = __shfl_xor_sync(0xffffffffu, lo[q], o);
-                two_sum_acc(hi[q], lo[q], bh, bl);
-            }
+        warp_two_sum_reduce<7>(hi, lo);
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
@@ -588,58 +414,10 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply, int per_pair)
     __syncthreads();
     if (warp == 0 && lane < STEP_CAMS) {
         const int kc = blockIdx.x * STEP_CAMS + lane;
-        double bl = 0.0;
-        if (kc < d.n_cams) {
-            double g[6];
-            bool ok = isfinite(s_hi[6][lane]);
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                g[q] = (double)s_hi[q][lane] + (double)s_lo[q][lane];
-                ok = ok && isfinite(g[q]);
-            }
-            if (!ok) atomicOr(d.err, ERR_NONFINITE);
-            bl = (double)s_hi[6][lane] + (double)s_lo[6][lane];
-            if (!apply) {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) d.grad[(size_t)kc * 6 + q] = g[q];
-            } else {
-                const float b1 = (float)s_hyper[2], b2 = (float)s_hyper[3], eps = (float)s_hyper[4];
-                const float lr_r = (float)s_hyper[0], lr_c = (float)s_hyper[1];
-                const float bc1 = 1.f - powf(b1, (float)t_step), bc2 = 1.f - powf(b2, (float)t_step);
-                double dl[6];
-                float mo[6], vo[6];
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const float gq = (float)g[q];
-                    mo[q] = b1 * s_mv[lane][q] + (1.f - b1) * gq;
-                    vo[q] = b2 * s_mv[lane][6 + q] + (1.f - b2) * gq * gq;
-                    dl[q] = (double)(-(q < 3 ? lr_r : lr_c) * (mo[q] / bc1) / (sqrtf(vo[q] / bc2) + eps));
-                }
-                double Ex[9], Rn[9], cn[3];
-                expmap64(dl, Ex);
-#pragma unroll
-                for (int r = 0; r < 3; ++r)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        Rn[3 * r + c] = Ex[3 * r] * s_Rc[lane][c] + Ex[3 * r + 1] * s_Rc[lane][3 + c] +
-                                        Ex[3 * r + 2] * s_Rc[lane][6 + c];
-                orthonormalize_rows(Rn);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) cn[q] = s_Rc[lane][9 + q] + dl[3 + q];
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const size_t o = (size_t)kc * 6 + q;
-                    d.m[o] = mo[q];
-                    d.v[o] = vo[q];
-                    d.grad[o] = g[q];
-                }
-#pragma unroll
-                for (int q = 0; q < 9; ++q) d.R[(size_t)kc * 9 + q] = Rn[q];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) d.c[(size_t)kc * 3 + q] = cn[q];
-                write_camrec(d.cam + (size_t)kc * CAMREC, Rn, cn);
-            }
-        }
+        const double bl = kc < d.n_cams
+            ? camera_update(d, kc, &s_hi[0][lane], &s_lo[0][lane], STEP_CAMS, s_mv[lane], s_Rc[lane], s_hyper,
+                            t_step, apply, d.cam + (size_t)kc * CAMREC)
+            : 0.0;
         s_loss[lane] = bl;
         __syncwarp(0xffu);
         if (lane == 0) {
@@ -699,10 +477,19 @@ __global__ void k_apply_gradient(DevProblem d) {
 
 __global__ void k_bump_step(DevProblem d) { *d.step += 1; }
 
-__global__ void __launch_bounds__(FIN_THREADS) k_finalize(DevProblem d, int n_blocks, int count_step) {
+// closes a chain of steps: loss of the last step and `count` steps added to the step count
+__global__ void __launch_bounds__(FIN_THREADS) k_finalize(DevProblem d, int n_blocks, int count) {
     pdl_wait();
     pdl_trigger();
-    finish_step(d, n_blocks, count_step);
+    finish_step(d, n_blocks, count);
+}
+
+// camera records copied back from the alternate buffer (one float4 per thread)
+__global__ void __launch_bounds__(256) k_copy_records(DevProblem d, const float4 *src) {
+    pdl_wait();
+    pdl_trigger();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < d.n_cams * (CAMREC / 4)) reinterpret_cast<float4 *>(d.cam)[i] = src[i];
 }
 
 // ---- launchers -------------------------------------------------------------------------------------
@@ -720,7 +507,14 @@ void launch_pair_setup(const DevProblem &d, cudaStream_t s, bool pdl, bool after
 }
 
 void launch_finalize(const DevProblem &d, bool count_step, cudaStream_t s, bool pdl) {
-    launch_k(k_finalize, dim3(1), dim3(FIN_THREADS), s, pdl, d, camera_step_blocks(d), count_step ? 1 : 0);
+    launch_finalize_n(d, count_step ? 1 : 0, nullptr, s, pdl);
+}
+
+void launch_finalize_n(const DevProblem &d, int count, const float *copy_src, cudaStream_t s, bool pdl) {
+    if (copy_src)
+        launch_k(k_copy_records, dim3(blocks_for((int64_t)d.n_cams * (CAMREC / 4), 256)), dim3(256), s, pdl, d,
+                 reinterpret_cast<const float4 *>(copy_src));
+    launch_k(k_finalize, dim3(1), dim3(FIN_THREADS), s, pdl, d, camera_step_blocks(d), count);
 }
 
 void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl) {
@@ -751,7 +545,7 @@ void launch_gather(const DevProblem &d, bool count_step, cudaStream_t s) {
     k_gather<<<blocks_for(d.n_cams, GATHER_THREADS) + 1, GATHER_THREADS, 0, s>>>(d, count_step ? 1 : 0);
 }
 
-static void loss_scales(const DevProblem &d, float &gscale, float &lscale) {
+void loss_scales(const DevProblem &d, float &gscale, float &lscale) {
     const double Z = d.z > 0.0 ? d.z : (double)d.n_pp;
     if (d.loss == FM_LOSS_IRLS) {  // stored weights are w * s
         gscale = (float)(2.0 / (Z * d.w_scale));
@@ -767,11 +561,11 @@ void launch_apply_gradient(const DevProblem &d, cudaStream_t s) {
     k_bump_step<<<1, 1, 0, s>>>(d);
 }
 
-void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl, bool per_pair) {
+void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl) {
     float gscale, lscale;
     loss_scales(d, gscale, lscale);
     launch_k(k_camera_step, dim3(blocks_for(d.n_cams, STEP_CAMS)), dim3(STEP_CAMS * 32), s, pdl, d,
-             gscale, lscale, apply ? 1 : 0, per_pair ? 1 : 0);
+             gscale, lscale, apply ? 1 : 0);
 }
 
 void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s) {

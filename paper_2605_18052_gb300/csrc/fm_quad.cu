@@ -15,7 +15,7 @@
 //   m2 = (x2^2, x2 y2, x2, y2^2, y2, 1),  m1 = (x1^2, x1 y1, x1, y1^2, y1, 1),
 // with W[3p+q][3r+s] = M[sym(p,r)][sym(q,s)], sym the index of the unordered pair in
 // (00, 01, 02, 11, 12, 22). Per point pair that is 36 multiply-adds instead of 45.
-#include "fm_walk.cuh"
+#include "fm_step.cuh"
 
 namespace fm {
 
@@ -120,15 +120,15 @@ __global__ void __launch_bounds__(CTA_WARPS * 32, 2) k_quad_accumulate(DevProble
     }
 }
 
-// per pair (one warp, a lane per sum): Kahan-sum the range partials; keep the anchor
-// e0 = E'_n of the geometry record. The records are stored component-major (entry q of pair n
-// at q * n_pairs + n), so that the per-iteration kernel reads them coalesced.
+// per pair (one warp, a lane per sum): Kahan-sum the range partials into the pair's record
+//   [0..35] M, [36] c0, [37..45] g0, [46..54] e0 = E'_n of the geometry record, [55] 0
+// (M first, so that the fused step reads it as 16-byte aligned vectors)
 __global__ void k_quad_combine(DevProblem d) {
     const int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (n >= d.n_pairs) return;
     const int r0 = d.pair_off[n] / WR, r1 = (d.pair_off[n + 1] - 1) / WR;
-    const size_t np = (size_t)d.n_pairs;
+    float *rec = d.quad + (size_t)n * QREC;
     for (int q = lane; q < QSUMS; q += 32) {
         float sum = 0.f, c = 0.f;
         for (int r = r0; r <= r1; ++r) {
@@ -137,60 +137,142 @@ __global__ void k_quad_combine(DevProblem d) {
             c = (t - sum) - y;
             sum = t;
         }
-        d.quad[q * np + n] = sum;
+        rec[q < 10 ? 36 + q : q - 10] = sum;
     }
-    if (lane < 9) d.quad[(QSUMS + lane) * np + n] = d.geo[(size_t)n * GEO + lane];
+    if (lane < 9) rec[46 + lane] = d.geo[(size_t)n * GEO + lane];
+    if (lane == 9) rec[55] = 0.f;
 }
 
-// one iteration's per-pair evaluation: geometry at the current poses, then the quadratic form;
-// writes the pair's sums (G'(9), loss) in the layout of the streaming partials
-constexpr int QPAIR_THREADS = 128;
-
-__global__ void __launch_bounds__(QPAIR_THREADS) k_quad_pair(DevProblem d, int prev_blocks) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = n < d.n_pairs ? d.cam_i[n] : 0, j = n < d.n_pairs ? d.cam_j[n] : 0;
-    pdl_wait();     // camera records of the previous step
-    pdl_trigger();
-    if (prev_blocks > 0 && blockIdx.x == 0) finish_step<QPAIR_THREADS>(d, prev_blocks, 1);
-    if (n >= d.n_pairs) return;
-    float e[9];
-    pair_geometry(d, n, i, j, e);
-    const size_t np = (size_t)d.n_pairs;
-    const float *Qn = d.quad + n;
-    auto Q = [&](int k) { return Qn[k * np]; };
-    float dv[9], q[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        dv[a] = e[a] - Q(QSUMS + a);
-        q[a] = Q(1 + a);
-    }
-    // q = g0 + W d, W[3p+q][3r+s] = M[sym(p,r)][sym(q,s)]
+// One optimiser iteration on the form, fused into one launch. Warp w owns camera
+// k = 8 * block + w; its lanes take the camera's image pairs, each computing the pair's
+// geometry from the two camera records (cam_src), the form's sums at the current E'_n,
+//   q = g0 + W d,  loss = c0 + d^T (g0 + q),  d = E'_n - e0,
+// and the chain rule to camera k. Both cameras of a pair evaluate it (O(1) each), which
+// removes a per-pair launch and the wait on it. The warp reduces with compensated butterflies,
+// then lanes 0..7 of warp 0 do the FP64 update of the block's cameras and write the new
+// records to cam_dst: the records of this step's poses stay intact in cam_src for the other
+// blocks. The Adam step count is *d.step + 1 + it; the launch that closes the chain adds
+// the chain's length to *d.step.
+__global__ void __launch_bounds__(STEP_CAMS * 32, 4)
+k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gscale, float lscale, int apply) {
+    __shared__ float s_hi[7][STEP_CAMS], s_lo[7][STEP_CAMS];
+    __shared__ float s_mv[STEP_CAMS][12];
+    __shared__ double s_Rc[STEP_CAMS][12];
+    __shared__ double s_hyper[5];
+    __shared__ double s_loss[STEP_CAMS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * STEP_CAMS + warp;
+    const int e_begin = k < d.n_cams ? d.cam_off[k] : 0;
+    const int e_end = k < d.n_cams ? d.cam_off[k + 1] : 0;
     constexpr int SYM[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-#pragma unroll
-    for (int u = 0; u < 6; ++u)
-#pragma unroll
-        for (int v = 0; v < 6; ++v) {
-            const float m = Q(10 + 6 * u + v);
-#pragma unroll
-            for (int p = 0; p < 3; ++p)
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    if (SYM[p][r] != u) continue;
-#pragma unroll
-                    for (int qq = 0; qq < 3; ++qq)
-#pragma unroll
-                        for (int ss = 0; ss < 3; ++ss)
-                            if (SYM[qq][ss] == v) q[3 * p + qq] = fmaf(m, dv[3 * r + ss], q[3 * p + qq]);
-                }
+    // the camera's first 32 (pair, role) entries and the pairs' cameras are static: fetch them
+    // while the previous step finishes
+    int e = e_begin + lane;
+    int n = 0, role = 0, ci = 0, cj = 0;
+    if (e < e_end) {
+        const int ent = d.cam_ent[e];
+        n = ent >> 1;
+        role = ent & 1;
+        ci = d.cam_i[n];
+        cj = d.cam_j[n];
+    }
+    pdl_wait();     // camera records, poses and moments of the previous step
+    pdl_trigger();
+    {
+        const int cam0 = blockIdx.x * STEP_CAMS;
+        for (int i = threadIdx.x; i < STEP_CAMS * 12; i += STEP_CAMS * 32) {
+            const int cc = i / 12, q = i % 12;
+            if (cam0 + cc < d.n_cams) {
+                s_mv[cc][q] = q < 6 ? d.m[(size_t)(cam0 + cc) * 6 + q] : d.v[(size_t)(cam0 + cc) * 6 + q - 6];
+                s_Rc[cc][q] = q < 9 ? d.R[(size_t)(cam0 + cc) * 9 + q] : d.c[(size_t)(cam0 + cc) * 3 + q - 9];
+            }
         }
-    // loss = c0 + d^T (g0 + q)
-    float loss = Q(0);
+        if (threadIdx.x < 5) s_hyper[threadIdx.x] = d.hyper[threadIdx.x];
+    }
+    const long long t_step = *d.step + 1 + it;
+    if (k < d.n_cams) {
+        float hi[7], lo[7];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) loss = fmaf(dv[a], Q(1 + a) + q[a], loss);
-    float4 *out = reinterpret_cast<float4 *>(d.pair_rec + (size_t)n * SLOT);
-    out[0] = make_float4(q[0], q[1], q[2], q[3]);
-    out[1] = make_float4(q[4], q[5], q[6], q[7]);
-    out[2] = make_float4(q[8], loss, 0.f, 0.f);
+        for (int q = 0; q < 7; ++q) hi[q] = lo[q] = 0.f;
+        for (; e < e_end; e += 32) {
+            if (e >= e_begin + 32) {
+                const int ent = d.cam_ent[e];
+                n = ent >> 1;
+                role = ent & 1;
+                ci = d.cam_i[n];
+                cj = d.cam_j[n];
+            }
+            float g[GEO];
+            if (!pair_geometry_regs(cam_src, d.cen, ci, cj, g)) atomicOr(d.err, ERR_DEGENERATE);
+            const float4 *rec = reinterpret_cast<const float4 *>(d.quad + (size_t)n * QREC);
+            float t[20];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                const float4 x = rec[9 + v];
+                t[4 * v] = x.x; t[4 * v + 1] = x.y; t[4 * v + 2] = x.z; t[4 * v + 3] = x.w;
+            }
+            // t[0] = c0, t[1..9] = g0, t[10..18] = e0
+            float dv[9], q[9];
+            float loss = t[0];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                dv[a] = g[a] - t[10 + a];
+                q[a] = t[1 + a];
+                loss = fmaf(dv[a], t[1 + a], loss);
+            }
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                const float4 x = rec[c];
+                const float mc[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int u = (4 * c + h) / 6, v = (4 * c + h) % 6;
+#pragma unroll
+                    for (int pp = 0; pp < 3; ++pp)
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) {
+                            if (SYM[pp][r] != u) continue;
+#pragma unroll
+                            for (int qq = 0; qq < 3; ++qq)
+#pragma unroll
+                                for (int ss = 0; ss < 3; ++ss)
+                                    if (SYM[qq][ss] == v) q[3 * pp + qq] = fmaf(mc[h], dv[3 * r + ss], q[3 * pp + qq]);
+                        }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 9; ++a) loss = fmaf(dv[a], q[a], loss);
+            const float sum[10] = {q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8], loss};
+            float contrib[7];
+            pair_chain_rule(g, role, sum, gscale, lscale, contrib);
+#pragma unroll
+            for (int w = 0; w < 7; ++w) two_sum_acc(hi[w], lo[w], contrib[w], 0.f);
+        }
+        warp_two_sum_reduce<7>(hi, lo);
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                s_hi[q][warp] = hi[q];
+                s_lo[q][warp] = lo[q];
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0 && lane < STEP_CAMS) {
+        const int kc = blockIdx.x * STEP_CAMS + lane;
+        const double bl = kc < d.n_cams
+            ? camera_update(d, kc, &s_hi[0][lane], &s_lo[0][lane], STEP_CAMS, s_mv[lane], s_Rc[lane], s_hyper,
+                            t_step, apply, cam_dst + (size_t)kc * CAMREC)
+            : 0.0;
+        s_loss[lane] = bl;
+        __syncwarp(0xffu);
+        if (lane == 0) {
+            double b = 0.0;
+#pragma unroll
+            for (int q = 0; q < STEP_CAMS; ++q) b += s_loss[q];
+            d.cam_loss[blockIdx.x] = b;
+        }
+    }
 }
 
 static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -209,9 +291,12 @@ void launch_quad_accumulate(const DevProblem &d, float tau, cudaStream_t s) {
     k_quad_combine<<<blocks_for(d.n_pairs, 8), 256, 0, s>>>(d);
 }
 
-void launch_quad_pair(const DevProblem &d, cudaStream_t s, bool pdl, bool after_step) {
-    launch_k(k_quad_pair, dim3(blocks_for(d.n_pairs, QPAIR_THREADS)), dim3(QPAIR_THREADS), s, pdl, d,
-             after_step ? camera_step_blocks(d) : 0);
+void launch_quad_step(const DevProblem &d, int it, const float *cam_src, float *cam_dst, bool apply,
+                      cudaStream_t s, bool pdl) {
+    float gscale, lscale;
+    loss_scales(d, gscale, lscale);
+    launch_k(k_quad_step, dim3(camera_step_blocks(d)), dim3(STEP_CAMS * 32), s, pdl, d, it, cam_src, cam_dst,
+             gscale, lscale, apply ? 1 : 0);
 }
 
 }  // namespace fm

@@ -1,0 +1,244 @@
+// Per-camera pieces shared by the optimiser-step kernels (the streaming path's camera step
+// and the quadratic form's fused step): compensated sums, the chain rule from an image pair's
+// sums to one of its cameras, and the FP64 Adam / exponential-map update of one camera.
+#pragma once
+
+#include <math.h>
+
+#include "fm_walk.cuh"
+
+namespace fm {
+
+constexpr int STEP_CAMS = 8;   // cameras (warps) per block of the step kernels
+
+// (hi, lo) += (bhi, blo) with the rounding error of the high parts kept (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float bhi, float blo) {
+    const float s = hi + bhi;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (bhi - bb);
+    const float l = lo + blo + err;
+    hi = s + l;
+    lo = l - (hi - s);
+}
+
+// ---- per camera: pose record --------------------------------------------------------------------
+__device__ __forceinline__ void write_camrec(float *rec, const double *R, const double *c) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) rec[i] = (float)R[i];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float hi = (float)c[q];
+        rec[9 + q] = hi;
+        rec[12 + q] = (float)(c[q] - (double)hi);
+    }
+    rec[15] = 0.f;
+}
+
+__device__ __forceinline__ void vee(const float *M, float *v) {
+    v[0] = M[7] - M[5];
+    v[1] = M[2] - M[6];
+    v[2] = M[3] - M[1];
+}
+
+// Exp(phi) by Rodrigues' formula, R = I + a K + b K^2 with K = [phi]_x. For |phi| < 0.1
+// (every Adam step: |phi| <= lr) a = sin(t)/t and b = (1 - cos(t))/t^2 come from their Taylor
+// series in t^2 through the t^8 terms (truncation < 3e-18, below half an FP64 ulp of 1),
+// which avoids FP64 sin/cos/sqrt/division on GB300's narrow FP64 pipe.
+__device__ __forceinline__ void expmap64(const double *phi, double *R) {
+    const double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
+    double a, b;
+    if (th2 < 0.01) {
+        a = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0))));
+        b = 0.5 * (1.0 - th2 * (1.0 / 12.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0) * (1.0 - th2 * (1.0 / 90.0)))));
+    } else {
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        a = sn / th;
+        b = (1.0 - cs) / th2;
+    }
+    const double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double k2 = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+            R[3 * r + c] = (r == c ? 1.0 : 0.0) + a * K[3 * r + c] + b * k2;
+        }
+}
+
+// 1/sqrt(x) in FP64: an FP32 seed refined by two Newton steps (the relative error squares
+// each step: ~2e-7 -> ~1e-13 -> below FP64 rounding)
+__device__ __forceinline__ double rsqrt64(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y;
+}
+
+// Gram-Schmidt on the rows: r0 normalised, r1 orthogonalised and normalised, r2 = r0 x r1
+__device__ __forceinline__ void orthonormalize_rows(double *R) {
+    const double n0 = rsqrt64(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+    for (int q = 0; q < 3; ++q) R[q] *= n0;
+    const double dp = R[0] * R[3] + R[1] * R[4] + R[2] * R[5];
+    for (int q = 0; q < 3; ++q) R[3 + q] -= dp * R[q];
+    const double n1 = rsqrt64(R[3] * R[3] + R[4] * R[4] + R[5] * R[5]);
+    for (int q = 0; q < 3; ++q) R[3 + q] *= n1;
+    R[6] = R[1] * R[5] - R[2] * R[4];
+    R[7] = R[2] * R[3] - R[0] * R[5];
+    R[8] = R[0] * R[4] - R[1] * R[3];
+}
+
+// Chain rule of one image pair (or one range partial of it) to one of its cameras.
+// gr = the pair's geometry record, sum[0..8] = sum s * o2 o1^T over the point pairs,
+// sum[9] = their loss terms. Writes the camera's 6 gradient components and (for the first
+// camera only) the loss.
+__device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const float *sum,
+                                                float gscale, float lscale, float *contrib) {
+    float Gp[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Gp[q] = sum[q] * gscale;
+    const float2 cen_i = make_float2(gr[22], gr[23]), cen_j = make_float2(gr[33], gr[34]);
+    float M[9], G[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        M[3 * a] = Gp[3 * a] + Gp[3 * a + 2] * cen_i.x;
+        M[3 * a + 1] = Gp[3 * a + 1] + Gp[3 * a + 2] * cen_i.y;
+        M[3 * a + 2] = Gp[3 * a + 2];
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        G[b] = M[b] + cen_j.x * M[6 + b];
+        G[3 + b] = M[3 + b] + cen_j.y * M[6 + b];
+        G[6 + b] = M[6 + b];
+    }
+    const float *Rn = gr + 9;
+    const float tn[3] = {gr[18], gr[19], gr[20]};
+    const float inv = gr[21];
+    const float *Rj = gr + 24;
+    const float th[3] = {tn[0] * inv, tn[1] * inv, tn[2] * inv};
+    float A[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        A[b] = -(-th[2] * G[3 + b] + th[1] * G[6 + b]);
+        A[3 + b] = -(th[2] * G[b] - th[0] * G[6 + b]);
+        A[6 + b] = -(-th[1] * G[b] + th[0] * G[3 + b]);
+    }
+    float GRt[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            GRt[3 * a + b] = G[3 * a] * Rn[3 * b] + G[3 * a + 1] * Rn[3 * b + 1] + G[3 * a + 2] * Rn[3 * b + 2];
+    float gth[3], gt[3], gc[3], gp[3];
+    vee(GRt, gth);
+    const float dp = th[0] * gth[0] + th[1] * gth[1] + th[2] * gth[2];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) gt[q] = (gth[q] - dp * th[q]) * inv;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) gc[q] = Rj[q] * gt[0] + Rj[3 + q] * gt[1] + Rj[6 + q] * gt[2];
+    if (role == 0) {
+        float RtA[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) RtA[3 * a + b] = Rn[a] * A[b] + Rn[3 + a] * A[3 + b] + Rn[6 + a] * A[6 + b];
+        vee(RtA, gp);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            contrib[q] = -gp[q];
+            contrib[3 + q] = gc[q];
+        }
+        contrib[6] = sum[9] * lscale;
+    } else {
+        float ARt[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) ARt[3 * a + b] = A[3 * a] * Rn[3 * b] + A[3 * a + 1] * Rn[3 * b + 1] + A[3 * a + 2] * Rn[3 * b + 2];
+        vee(ARt, gp);
+        contrib[0] = gp[0] + (tn[1] * gt[2] - tn[2] * gt[1]);
+        contrib[1] = gp[1] + (tn[2] * gt[0] - tn[0] * gt[2]);
+        contrib[2] = gp[2] + (tn[0] * gt[1] - tn[1] * gt[0]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) contrib[3 + q] = -gc[q];
+        contrib[6] = 0.f;
+    }
+}
+
+
+// warp-wide TwoSum butterfly of N (hi, lo) pairs: every lane ends with the total
+template <int N>
+__device__ __forceinline__ void warp_two_sum_reduce(float *hi, float *lo) {
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, hi[q], o);
+            const float bl = __shfl_xor_sync(0xffffffffu, lo[q], o);
+            two_sum_acc(hi[q], lo[q], bh, bl);
+        }
+}
+
+// Phase 2 of a step for camera kc, one lane: the FP64 sum of the gradient's hi + lo parts, then
+// either the gradient is written (apply = 0) or one Adam step (FP32 moments) with the FP64
+// exponential map, re-orthonormalisation and centre update, and the new camera record at
+// rec_out. hi/lo hold 7 values (6 gradient components, the loss) `stride` apart; mv = the
+// camera's Adam m (6) and v (6); Rc = its R (9) and c (3); hyper = lr_rot, lr_c, beta1, beta2,
+// eps. Returns the camera's loss share.
+__device__ __forceinline__ double camera_update(const DevProblem &d, int kc, const float *hi, const float *lo,
+                                                int stride, const float *mv, const double *Rc,
+                                                const double *hyper, long long t_step, int apply,
+                                                float *rec_out) {
+    double g[6];
+    bool ok = isfinite(hi[6 * stride]);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        g[q] = (double)hi[q * stride] + (double)lo[q * stride];
+        ok = ok && isfinite(g[q]);
+    }
+    if (!ok) atomicOr(d.err, ERR_NONFINITE);
+    const double bl = (double)hi[6 * stride] + (double)lo[6 * stride];
+    if (!apply) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) d.grad[(size_t)kc * 6 + q] = g[q];
+        return bl;
+    }
+    const float b1 = (float)hyper[2], b2 = (float)hyper[3], eps = (float)hyper[4];
+    const float lr_r = (float)hyper[0], lr_c = (float)hyper[1];
+    const float bc1 = 1.f - powf(b1, (float)t_step), bc2 = 1.f - powf(b2, (float)t_step);
+    double dl[6];
+    float mo[6], vo[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float gq = (float)g[q];
+        mo[q] = b1 * mv[q] + (1.f - b1) * gq;
+        vo[q] = b2 * mv[6 + q] + (1.f - b2) * gq * gq;
+        dl[q] = (double)(-(q < 3 ? lr_r : lr_c) * (mo[q] / bc1) / (sqrtf(vo[q] / bc2) + eps));
+    }
+    double Ex[9], Rn[9], cn[3];
+    expmap64(dl, Ex);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            Rn[3 * r + c] = Ex[3 * r] * Rc[c] + Ex[3 * r + 1] * Rc[3 + c] + Ex[3 * r + 2] * Rc[6 + c];
+    orthonormalize_rows(Rn);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cn[q] = Rc[9 + q] + dl[3 + q];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const size_t o = (size_t)kc * 6 + q;
+        d.m[o] = mo[q];
+        d.v[o] = vo[q];
+        d.grad[o] = g[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) d.R[(size_t)kc * 9 + q] = Rn[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) d.c[(size_t)kc * 3 + q] = cn[q];
+    write_camrec(rec_out, Rn, cn);
+    return bl;
+}
+
+}  // namespace fm

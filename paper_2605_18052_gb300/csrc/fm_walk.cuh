@@ -209,13 +209,14 @@ __device__ __forceinline__ void load_camrec(const float *rec, float *R, float *h
 }
 
 
-// Relative pose and centroid-folded essential matrix of pair n = (i, j), written to its
-// geometry record: E'_n = T_j^T [t_n/|t_n|]_x R_n T_i, R_n = R_j R_i^T, t_n = R_j (c_i - c_j).
-// E_out (optional): receives E'_n as well.
-__device__ __forceinline__ void pair_geometry(const DevProblem &d, int n, int i, int j, float *E_out = nullptr) {
+// Relative pose and centroid-folded essential matrix of the pair (i, j) from the camera
+// records `cam` into the geometry record g (registers): E'_n = T_j^T [t_n/|t_n|]_x R_n T_i,
+// R_n = R_j R_i^T, t_n = R_j (c_i - c_j). Returns false (and g with 1/|t_n| = 0) when the
+// baseline is degenerate.
+__device__ __forceinline__ bool pair_geometry_regs(const float *cam, const float2 *cen, int i, int j, float *g) {
     float Ri[9], Rj[9], hi_i[3], lo_i[3], hi_j[3], lo_j[3], dc[3];
-    load_camrec(d.cam + (size_t)i * CAMREC, Ri, hi_i, lo_i);
-    load_camrec(d.cam + (size_t)j * CAMREC, Rj, hi_j, lo_j);
+    load_camrec(cam + (size_t)i * CAMREC, Ri, hi_i, lo_i);
+    load_camrec(cam + (size_t)j * CAMREC, Rj, hi_j, lo_j);
     // c_i - c_j from the two-float representation: the high parts of nearby centres
     // subtract exactly, so the baseline keeps FP32 relative accuracy far from the origin
 #pragma unroll
@@ -235,12 +236,8 @@ __device__ __forceinline__ void pair_geometry(const DevProblem &d, int n, int i,
 #pragma unroll
     for (int q = 0; q < 3; ++q) cmax = fmaxf(cmax, fmaxf(fabsf(hi_i[q]), fabsf(hi_j[q])));
     const float floor2 = 1e-20f * cmax * cmax;
-    float inv = 0.f;
-    if (nt2 > floor2 && isfinite(nt2)) {
-        inv = 1.0f / sqrtf(nt2);
-    } else {
-        atomicOr(d.err, ERR_DEGENERATE);
-    }
+    const bool ok = nt2 > floor2 && isfinite(nt2);
+    const float inv = ok ? 1.0f / sqrtf(nt2) : 0.f;
     const float th[3] = {tn[0] * inv, tn[1] * inv, tn[2] * inv};
     // E = [th]_x R_n
     float E[9];
@@ -251,8 +248,7 @@ __device__ __forceinline__ void pair_geometry(const DevProblem &d, int n, int i,
         E[6 + b] = -th[1] * Rn[b] + th[0] * Rn[3 + b];
     }
     // E' = T_j^T E T_i with T = [[1,0,cx],[0,1,cy],[0,0,1]] (keypoints stored as offsets o = x - c)
-    const float2 cen_i = d.cen[i], cen_j = d.cen[j];
-    float g[GEO];
+    const float2 cen_i = cen[i], cen_j = cen[j];
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         g[3 * a] = E[3 * a];
@@ -276,6 +272,14 @@ __device__ __forceinline__ void pair_geometry(const DevProblem &d, int n, int i,
     g[33] = cen_j.x;
     g[34] = cen_j.y;
     g[35] = 0.f;
+    return ok;
+}
+
+// the geometry record of pair n = (i, j) at the current camera records, written to d.geo
+// (E_out, optional, receives E'_n as well)
+__device__ __forceinline__ void pair_geometry(const DevProblem &d, int n, int i, int j, float *E_out = nullptr) {
+    float g[GEO];
+    if (!pair_geometry_regs(d.cam, d.cen, i, j, g)) atomicOr(d.err, ERR_DEGENERATE);
     if (E_out) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) E_out[k] = g[k];
@@ -285,14 +289,14 @@ __device__ __forceinline__ void pair_geometry(const DevProblem &d, int n, int i,
     for (int k = 0; k < GEO / 4; ++k) out[k] = make_float4(g[4 * k], g[4 * k + 1], g[4 * k + 2], g[4 * k + 3]);
 }
 
-// Loss total of a camera-step launch (FP64, fixed order over its blocks) and, after an
-// optimiser step, the step count. One block of NT threads (NT divides FIN_THREADS); the
+// Loss total of a camera-step launch (FP64, fixed order over its blocks) and `count` steps
+// added to the step count. One block of NT threads (NT divides FIN_THREADS); the
 // summation order is that of FIN_THREADS threads whatever NT is, so every launch that
 // finishes a step produces the same bits.
 constexpr int FIN_THREADS = 256;
 
 template <int NT = FIN_THREADS>
-__device__ __forceinline__ void finish_step(const DevProblem &d, int n_blocks, int count_step) {
+__device__ __forceinline__ void finish_step(const DevProblem &d, int n_blocks, int count) {
     static_assert(FIN_THREADS % NT == 0, "block must divide FIN_THREADS");
     __shared__ double red[FIN_THREADS];
 #pragma unroll
@@ -308,7 +312,7 @@ __device__ __forceinline__ void finish_step(const DevProblem &d, int n_blocks, i
     }
     if (threadIdx.x == 0) {
         *d.loss_out = red[0];
-        if (count_step) *d.step += 1;
+        *d.step += count;
     }
 }
 
