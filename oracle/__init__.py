@@ -190,8 +190,7 @@ def irls_weights(eps_hat, tau: float, delta: float):
 
 def threshold_schedule(r: int, tau0: float, tau_min: float, factor: float = 0.8) -> float:
     """Filtering threshold of round r: starts large and shrinks by `factor` each round down to
-    a floor ("a relatively large initial threshold ... gradually decrease to a pre-determined
-    minimum")."""
+    a fixed floor (filtering paragraph of Sec. "Epipolar Adjustment", which gives no values)."""
     return max(tau_min, tau0 * factor ** r)
 
 
