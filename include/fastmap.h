@@ -292,6 +292,62 @@ FM_API fm_status fm_synchronize(fm_problem *p);
 FM_API fm_status fm_enable_kernel_timing(fm_problem *p, int32_t enable);
 FM_API fm_status fm_kernel_time(fm_problem *p, double *ms, int64_t *launches);
 
+/* ---- global translation (Sec. "Global Translation") ----------------------------------------------
+ * With the world-to-camera rotations R_k fixed and a unit relative translation t_{i->j} per
+ * image pair (in camera j's frame), the world direction from camera i's centre to camera j's
+ * is o_{i->j} = -R_j^T t_{i->j}, and the centres o_k minimise
+ *   L_t = (1/|P|) sum_n || (o_j - o_i)/||o_j - o_i|| - o_{i->j} ||_1
+ * (Eq. fastmap-global-translation-objective). Several runs from random initial centres are
+ * advanced together and merged (paragraph "Multiple initializations"): every run is centred
+ * at the origin and scaled to unit mean norm, and each camera takes its centre from the run in
+ * which the mean of its pairs' L1 terms is lowest (the lower run index on ties); the merged
+ * centres continue as one run with fresh Adam state.
+ * Numerics: centres and their update FP64; per-pair terms FP32 from the FP64 difference of the
+ * two centres; subgradient of |x| at 0 is 0; per-camera sums FP32 in a fixed order; loss FP64.
+ */
+typedef struct fm_translation fm_translation;
+
+typedef struct {
+    double lr;          /* Adam step size (units of the centres; 1e-2) */
+    double beta1;       /* 0.9 */
+    double beta2;       /* 0.999 */
+    double adam_eps;    /* 1e-12 */
+    int32_t use_graph;  /* 1: replay CUDA graphs of chained iterations */
+    int32_t reserved;
+} fm_translation_options;
+
+FM_API void fm_translation_default_options(fm_translation_options *opt);
+/*
+ * n_cams >= 2 cameras with rotations R (host FP64 n_cams x 9, row-major, world-to-camera);
+ * n_pairs >= 1 image pairs (cam_i, cam_j host int32, distinct, in range) with unit relative
+ * translations t_rel (host FP64 n_pairs x 3, |t| = 1 within 1e-6); n_runs (1..65535) initial
+ * centre sets o_init (host FP64 n_runs x n_cams x 3, drawn by the caller). Everything is
+ * copied; work runs on a private stream ordered after and before `stream` (a cudaStream_t).
+ * FM_EINVAL on bad arguments.
+ */
+FM_API fm_status fm_translation_create(int32_t n_cams, const double *R, int32_t n_pairs,
+                                       const int32_t *cam_i, const int32_t *cam_j,
+                                       const double *t_rel, int32_t n_runs, const double *o_init,
+                                       const fm_translation_options *opt, void *stream,
+                                       fm_translation **out);
+FM_API void fm_translation_destroy(fm_translation *tp);
+/* Number of runs currently advanced (n_runs, or 1 after fm_translation_merge). */
+FM_API int32_t fm_translation_num_runs(const fm_translation *tp);
+/* Per run (host outputs): loss[runs]; grad[runs x n_cams x 3] and cam_loss[runs x n_cams]
+ * (mean L1 term of each camera's pairs, 0 for a camera in no pair) may be NULL. Synchronises;
+ * FM_EDEGENERATE if two cameras of a pair share a centre. */
+FM_API fm_status fm_translation_loss_grad(fm_translation *tp, double *loss, double *grad,
+                                          double *cam_loss);
+/* n_iters Adam iterations of every run. Asynchronous. */
+FM_API fm_status fm_translation_step(fm_translation *tp, int32_t n_iters);
+/* Merge the runs into one (see above); the merged centres are normalised. Synchronises. */
+FM_API fm_status fm_translation_merge(fm_translation *tp);
+FM_API fm_status fm_translation_set_learning_rate(fm_translation *tp, double lr);
+/* Centres of the current runs (host FP64 runs x n_cams x 3). Synchronises. */
+FM_API fm_status fm_translation_get_centres(fm_translation *tp, double *o);
+/* Replace the centres of the current runs (host, same layout) and reset the Adam state. */
+FM_API fm_status fm_translation_set_centres(fm_translation *tp, const double *o);
+
 /*
  * Loss and gradient without any device allocation, for callers that cannot call cudaMalloc:
  * code whose device memory is owned by another memory manager (a framework's caching

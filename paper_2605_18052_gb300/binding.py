@@ -26,6 +26,9 @@ EXPORTED = [
     "fm_mlp_get_params", "fm_mlp_set_params", "fm_mlp_train_step", "fm_mlp_gradient", "fm_mlp_forward",
     "fm_set_scores", "fm_collect_features", "fm_learned_weights", "fm_reset_history",
     "fm_preaggregate", "fm_irls_preaggregate", "fm_loss_grad_quadratic", "fm_step_quadratic",
+    "fm_translation_default_options", "fm_translation_create", "fm_translation_destroy",
+    "fm_translation_num_runs", "fm_translation_loss_grad", "fm_translation_step", "fm_translation_merge",
+    "fm_translation_set_learning_rate", "fm_translation_get_centres", "fm_translation_set_centres",
 ]
 
 
@@ -105,6 +108,16 @@ def load_library(path: str = LIB_PATH):
         "fm_irls_preaggregate": (I32, [P, D, P]),
         "fm_loss_grad_quadratic": (I32, [P, P, P]),
         "fm_step_quadratic": (I32, [P, I32]),
+        "fm_translation_default_options": (None, [P]),
+        "fm_translation_create": (I32, [I32, P, I32, P, P, P, I32, P, P, P, P]),
+        "fm_translation_destroy": (None, [P]),
+        "fm_translation_num_runs": (I32, [P]),
+        "fm_translation_loss_grad": (I32, [P, P, P, P]),
+        "fm_translation_step": (I32, [P, I32]),
+        "fm_translation_merge": (I32, [P]),
+        "fm_translation_set_learning_rate": (I32, [P, D]),
+        "fm_translation_get_centres": (I32, [P, P]),
+        "fm_translation_set_centres": (I32, [P, P]),
         "fm_status_string": (ctypes.c_char_p, [I32]),
         "fm_last_error": (ctypes.c_char_p, []),
     }
@@ -374,6 +387,89 @@ class Problem:
         n = ctypes.c_int64()
         _check(load_library().fm_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+
+class TranslationOptions(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("adam_eps", ctypes.c_double), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def translation_options(**kw) -> TranslationOptions:
+    o = TranslationOptions()
+    load_library().fm_translation_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Translation:
+    """Global translation stage on the GPU (fm_translation_*): camera centres from unit
+    relative translations with the rotations fixed, several runs from given initial centres,
+    their merge and the final run."""
+
+    def __init__(self, R, cam_i, cam_j, t_rel, o_init, options: TranslationOptions | None = None, stream=None):
+        lib = load_library()
+        R = _host(R, np.float64).reshape(-1, 9)
+        ci = _host(cam_i, np.int32).reshape(-1)
+        cj = _host(cam_j, np.int32).reshape(-1)
+        t = _host(t_rel, np.float64).reshape(-1, 3)
+        o0 = _host(o_init, np.float64)
+        self.n_cams, self.n_pairs = R.shape[0], ci.shape[0]
+        o0 = o0.reshape(-1, self.n_cams, 3)
+        h = ctypes.c_void_p()
+        _check(lib.fm_translation_create(self.n_cams, _ptr(R), self.n_pairs, _ptr(ci), _ptr(cj), _ptr(t),
+                                         o0.shape[0], _ptr(np.ascontiguousarray(o0)),
+                                         ctypes.byref(options) if options is not None else None,
+                                         stream if stream is not None else _current_stream(), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().fm_translation_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n_runs(self) -> int:
+        return load_library().fm_translation_num_runs(self._h)
+
+    def loss_grad(self):
+        """(loss (runs,), gradient (runs, n_cams, 3), camera losses (runs, n_cams))."""
+        r = self.n_runs
+        loss = np.empty(r)
+        g = np.empty((r, self.n_cams, 3))
+        cl = np.empty((r, self.n_cams))
+        _check(load_library().fm_translation_loss_grad(self._h, _ptr(loss), _ptr(g), _ptr(cl)))
+        return loss, g, cl
+
+    def step(self, n_iters: int = 1):
+        _check(load_library().fm_translation_step(self._h, int(n_iters)))
+
+    def merge(self):
+        _check(load_library().fm_translation_merge(self._h))
+
+    def set_learning_rate(self, lr: float):
+        _check(load_library().fm_translation_set_learning_rate(self._h, float(lr)))
+
+    def centres(self) -> np.ndarray:
+        out = np.empty((self.n_runs, self.n_cams, 3))
+        _check(load_library().fm_translation_get_centres(self._h, _ptr(out)))
+        return out
+
+    def set_centres(self, o):
+        o = np.ascontiguousarray(_host(o, np.float64).reshape(self.n_runs, self.n_cams, 3))
+        _check(load_library().fm_translation_set_centres(self._h, _ptr(o)))
 
 
 class Mlp:

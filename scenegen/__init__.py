@@ -478,3 +478,26 @@ def perturb_poses(R, t, cam_i, cam_j, rot_deg: float, trans_frac: float, g, kind
     C0 = C + mag * _random_unit(n, g, device)
     t0 = -torch.einsum("nab,nb->na", R0, C0)
     return R0, t0
+
+
+def relative_translations(sc: Scene, noise_deg: float = 1.0, outlier_frac: float = 0.05, seed: int = 0):
+    """Unit relative translations of the scene's image pairs as a relative-pose step would
+    deliver them: t_{i->j} = R_j (c_i - c_j) / |c_i - c_j| from the true poses, turned by a
+    random angle of about `noise_deg` degrees, and for a fraction `outlier_frac` of the pairs
+    replaced by a uniform random direction. Returns (t_rel (B, 3) float64, outlier mask)."""
+    g = torch.Generator(device="cpu")
+    g.manual_seed(int(seed) * 7919 + 17)
+    R = sc.R_gt.detach().cpu().to(F64)
+    t = sc.t_gt.detach().cpu().to(F64)
+    C = -torch.einsum("nba,nb->na", R, t)
+    ci, cj = sc.cam_i.detach().cpu().long(), sc.cam_j.detach().cpu().long()
+    d = torch.einsum("nab,nb->na", R[cj], C[ci] - C[cj])
+    d = d / torch.linalg.norm(d, dim=-1, keepdim=True)
+    B = d.shape[0]
+    axis = _random_unit(B, g, torch.device("cpu"))
+    ang = math.radians(noise_deg) * torch.randn(B, 1, dtype=F64, generator=g)
+    d = torch.einsum("nab,nb->na", rotation_exp(axis * ang), d)
+    out = torch.rand(B, dtype=F64, generator=g) < outlier_frac
+    d[out] = _random_unit(int(out.sum()), g, torch.device("cpu"))
+    d = d / torch.linalg.norm(d, dim=-1, keepdim=True)
+    return d.numpy(), out.numpy()

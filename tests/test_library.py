@@ -49,9 +49,10 @@ def test_build_flags_target_sm_103a():
 
 
 def test_public_python_surface():
-    for name in ["Problem", "Mlp", "Schedule", "refine", "epipolar_loss", "EpipolarLoss", "default_options"]:
+    for name in ["Problem", "Mlp", "Translation", "Schedule", "refine", "epipolar_loss", "EpipolarLoss",
+                 "default_options", "translation_options"]:
         assert hasattr(fm, name), name
-    from paper_2605_18052_gb300 import learned, metrics  # noqa: F401
+    from paper_2605_18052_gb300 import learned, metrics, translation  # noqa: F401
 
 
 def test_default_options(lib):
@@ -82,3 +83,23 @@ def test_create_rejects_bad_host_arguments_without_a_gpu(lib):
         fm.Problem(R, t, [0], [1], pid, x, x, options=fm.default_options(delta=0.0))
     with pytest.raises(fm.FastMapError):
         fm.Problem(R, t, [0], [1], pid, x, x, options=fm.default_options(beta1=1.0))
+
+
+def test_translation_rejects_bad_host_arguments_without_a_gpu(lib):
+    R = np.tile(np.eye(3), (3, 1, 1))
+    t = np.array([[1.0, 0, 0], [0.0, 1.0, 0]])
+    o = np.zeros((2, 3, 3))
+    good = dict(R=R, cam_i=[0, 1], cam_j=[1, 2], t_rel=t, o_init=o)
+    cases = [
+        dict(good, cam_j=[1, 1], cam_i=[1, 0]),                # cam_i == cam_j
+        dict(good, cam_j=[1, 3]),                             # camera index out of range
+        dict(good, t_rel=2.0 * t),                            # not unit length
+        dict(good, o_init=np.full((2, 3, 3), np.nan)),        # non-finite centres
+        dict(good, R=R[:1], cam_i=[0], cam_j=[0], t_rel=t[:1], o_init=o[:, :1]),  # n_cams < 2
+    ]
+    for c in cases:
+        with pytest.raises(fm.FastMapError) as ei:
+            fm.Translation(c["R"], c["cam_i"], c["cam_j"], c["t_rel"], c["o_init"])
+        assert ei.value.status == -1
+    with pytest.raises(fm.FastMapError):
+        fm.Translation(R, [0, 1], [1, 2], t, o, fm.translation_options(lr=0.0))
