@@ -233,6 +233,50 @@ def translation_section(sc, stream, runs: int = 8, iters: int = 1000, final_iter
                     "unfold within the iteration budget, on the 128-camera sphere they do"}
 
 
+def rotation_section(sc, stream, iters: int = 500):
+    """Global rotation on the scene's image pairs (relative rotations with 1 deg noise; pairs
+    with wrong relative rotations are filtered upstream in the pipeline): column-wise
+    initialisation (conjugate gradients), then `iters` Adam steps on the geodesic objective.
+    The robustness to wrong pairs is shown on the 128-camera sphere with 5% of them."""
+    import numpy as np
+    import torch
+    import scenegen
+    import paper_2605_18052_gb300 as fm
+    from paper_2605_18052_gb300 import metrics
+
+    def run(scene, outliers, timed):
+        Rrel, _ = scenegen.relative_rotations(scene, 1.0, outliers, 0)
+        Rg = scene.R_gt.cpu().numpy()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with fm.Rotation(scene.cam_i.cpu().numpy(), scene.cam_j.cpu().numpy(), Rrel, scene.n_cams,
+                         fm.rotation_options(lr=1e-3), stream=stream.cuda_stream) as rp:
+            if timed:
+                rp.initialize()             # warm-up
+                rp.step(16)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            cg_iters, cg_res = rp.initialize()
+            ev[1].record(stream)
+            e0 = float(metrics.rotation_error_deg(rp.rotations(), Rg).mean())
+            torch.cuda.synchronize()
+            ev[2].record(stream)
+            rp.step(iters)
+            ev[3].record(stream)
+            R1 = rp.rotations()
+        torch.cuda.synchronize()
+        e1 = float(metrics.rotation_error_deg(R1, Rg).mean())
+        it_ms = ev[2].elapsed_time(ev[3])
+        return {"pairs": scene.n_pairs, "cameras": scene.n_cams, "wrong_pairs": outliers,
+                "init_ms": ev[0].elapsed_time(ev[1]), "cg_iterations": cg_iters,
+                "cg_relative_residual": cg_res, "init_rotation_error_deg": e0, "iters": iters,
+                "iteration_us": it_ms / iters * 1e3, "pair_terms_per_s": scene.n_pairs * iters / (it_ms * 1e-3),
+                "refined_rotation_error_deg": e1}
+
+    out = run(sc, 0.0, True)
+    out["sphere128_5pct_wrong_pairs"] = run(scenegen.make_scene("sphere128", seed=0), 0.05, False)
+    return out
+
+
 def cpu_oracle_rate(sc, seconds: float):
     """FP64 oracle loss+gradient on a bounded sample of whole image pairs (1 thread)."""
     import numpy as np
@@ -372,10 +416,12 @@ def main():
                 "kernel": f"k_stream_loss<{args.storage.upper()}, IRLS>",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs burst copy)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6}
-    # global translation stage on the same scene's image pairs (8 runs from random centres)
-    trans = None
+    # global translation stage on the same scene's image pairs (8 runs from random centres),
+    # global rotation stage on them (initialisation + refinement)
+    trans = rot = None
     if rank == 0 and not args.no_translation:
         trans = translation_section(sc, stream)
+        rot = rotation_section(sc, stream)
 
     # per step: reweighting (pair setup + weights), 3 launches per iteration, and one finalize per
     # graph launch (graphs of 8 chained iterations, then single iterations)
@@ -464,6 +510,7 @@ def main():
                           "parallelism": f"replicas x{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "time_to_accuracy": tta, "quadratic_path": quad, "global_translation": trans,
+               "global_rotation": rot,
                "clocks": clocks, "hbm_frac_of_step": value * 1e9 * bytes_per_launch / n_pp / 1e9 / peak}
         print(json.dumps(out))
     if world > 1:

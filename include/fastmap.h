@@ -348,6 +348,59 @@ FM_API fm_status fm_translation_get_centres(fm_translation *tp, double *o);
 /* Replace the centres of the current runs (host, same layout) and reset the Adam state. */
 FM_API fm_status fm_translation_set_centres(fm_translation *tp, const double *o);
 
+/* ---- global rotation (Sec. "Global Rotation") -----------------------------------------------------
+ * World-to-camera rotations R_k from relative rotations R_{i->j} of the image pairs, minimising
+ *   L_R = (1/|P|) sum_n d(R_j, R_{i->j} R_i),   d(R, R') = arccos((tr(R^T R') - 1)/2)
+ * (Eq. fastmap-rotation-objective) with every R_k in the 6D representation (a1, a2): columns
+ * b1 = a1/|a1|, b2 = the normalised part of a2 orthogonal to b1, b3 = b1 x b2.
+ * Initialisation (paragraph "Initialization details", column-wise least squares): column 1
+ * from min sum ||x_j - R_{i->j} x_i||^2, column 2 from min (1/|P|) sum ||y_j - R_{i->j} y_i||^2
+ * + (1/N) sum (x_k^T y_k)^2, each with camera 0's column held at e1 / e2 (gauge: R_0 = I), solved
+ * by preconditioned conjugate gradients on the GPU; columns normalised, column 2 orthogonalised
+ * to column 1, column 3 their cross product. All FP64; for the gradient the arccos argument is
+ * clamped to 1 - 1e-12 (finite at d = 0).
+ */
+typedef struct fm_rotation fm_rotation;
+
+typedef struct {
+    double lr;            /* Adam step size on the 6D parameters (1e-3) */
+    double beta1;         /* 0.9 */
+    double beta2;         /* 0.999 */
+    double adam_eps;      /* 1e-12 */
+    double cg_tol;        /* stop when the preconditioned residual norm falls by this factor (1e-9) */
+    int32_t cg_max_iters; /* per column system (20000) */
+    int32_t use_graph;    /* 1: replay CUDA graphs of chained iterations */
+} fm_rotation_options;
+
+FM_API void fm_rotation_default_options(fm_rotation_options *opt);
+/*
+ * n_cams >= 2, n_pairs >= 1 image pairs (cam_i, cam_j host int32, distinct, in range) forming a
+ * connected graph, relative rotations R_rel (host FP64 n_pairs x 9, row-major, orthonormal with
+ * det +1 within 1e-6, mapping camera i's frame to camera j's). Copied. FM_EINVAL otherwise.
+ */
+FM_API fm_status fm_rotation_create(int32_t n_cams, int32_t n_pairs, const int32_t *cam_i,
+                                    const int32_t *cam_j, const double *R_rel,
+                                    const fm_rotation_options *opt, void *stream,
+                                    fm_rotation **out);
+FM_API void fm_rotation_destroy(fm_rotation *rp);
+/* The column-wise initialisation; resets the Adam state. Writes the total number of conjugate-
+ * gradient iterations and the worse relative residual of the two systems (either may be NULL).
+ * Synchronises; FM_EDEGENERATE if a solved column vanishes. */
+FM_API fm_status fm_rotation_initialize(fm_rotation *rp, int32_t *cg_iters, double *cg_residual);
+/* L_R (host scalar) and its gradient with respect to the 6D parameters (host n_cams x 6,
+ * may be NULL). Synchronises. */
+FM_API fm_status fm_rotation_loss_grad(fm_rotation *rp, double *loss, double *grad6);
+/* n_iters Adam iterations on the 6D parameters. Asynchronous. */
+FM_API fm_status fm_rotation_step(fm_rotation *rp, int32_t n_iters);
+FM_API fm_status fm_rotation_set_learning_rate(fm_rotation *rp, double lr);
+/* Rotations (host FP64 n_cams x 9) / 6D parameters (n_cams x 6) of the current state. */
+FM_API fm_status fm_rotation_get_rotations(fm_rotation *rp, double *R);
+FM_API fm_status fm_rotation_get_params(fm_rotation *rp, double *a6);
+/* Replace the state by rotations (their first two columns become the parameters) or by 6D
+ * parameters; resets the Adam state. */
+FM_API fm_status fm_rotation_set_rotations(fm_rotation *rp, const double *R);
+FM_API fm_status fm_rotation_set_params(fm_rotation *rp, const double *a6);
+
 /*
  * Loss and gradient without any device allocation, for callers that cannot call cudaMalloc:
  * code whose device memory is owned by another memory manager (a framework's caching

@@ -15,7 +15,9 @@ Gram-Schmidt-orthogonalised to column 1; column 3 = column 1 x column 2.
 
 Readings where the thesis is silent: the least-squares problems fix the gauge (a global
 rotation) and exclude the zero solution by holding camera 0's column at its value for
-R_0 = I (e1, then e2); they are solved exactly here (sparse direct solve). For the gradient the
+R_0 = I (e1, then e2); they are solved exactly here (sparse direct solve). (With inconsistent
+relative rotations this anchored solution shrinks with the distance from camera 0; on long
+chains with wrong pairs it can vanish, which the thesis' upstream pair filtering avoids.) For the gradient the
 arccos argument is clamped to 1 - 1e-12, so it stays finite at d = 0. The optimiser is
 Adam on the 6D parameters with a constant step size. Plain FP64 NumPy/SciPy.
 """

@@ -29,6 +29,9 @@ EXPORTED = [
     "fm_translation_default_options", "fm_translation_create", "fm_translation_destroy",
     "fm_translation_num_runs", "fm_translation_loss_grad", "fm_translation_step", "fm_translation_merge",
     "fm_translation_set_learning_rate", "fm_translation_get_centres", "fm_translation_set_centres",
+    "fm_rotation_default_options", "fm_rotation_create", "fm_rotation_destroy", "fm_rotation_initialize",
+    "fm_rotation_loss_grad", "fm_rotation_step", "fm_rotation_set_learning_rate", "fm_rotation_get_rotations",
+    "fm_rotation_get_params", "fm_rotation_set_rotations", "fm_rotation_set_params",
 ]
 
 
@@ -118,6 +121,17 @@ def load_library(path: str = LIB_PATH):
         "fm_translation_set_learning_rate": (I32, [P, D]),
         "fm_translation_get_centres": (I32, [P, P]),
         "fm_translation_set_centres": (I32, [P, P]),
+        "fm_rotation_default_options": (None, [P]),
+        "fm_rotation_create": (I32, [I32, I32, P, P, P, P, P, P]),
+        "fm_rotation_destroy": (None, [P]),
+        "fm_rotation_initialize": (I32, [P, P, P]),
+        "fm_rotation_loss_grad": (I32, [P, P, P]),
+        "fm_rotation_step": (I32, [P, I32]),
+        "fm_rotation_set_learning_rate": (I32, [P, D]),
+        "fm_rotation_get_rotations": (I32, [P, P]),
+        "fm_rotation_get_params": (I32, [P, P]),
+        "fm_rotation_set_rotations": (I32, [P, P]),
+        "fm_rotation_set_params": (I32, [P, P]),
         "fm_status_string": (ctypes.c_char_p, [I32]),
         "fm_last_error": (ctypes.c_char_p, []),
     }
@@ -470,6 +484,91 @@ class Translation:
     def set_centres(self, o):
         o = np.ascontiguousarray(_host(o, np.float64).reshape(self.n_runs, self.n_cams, 3))
         _check(load_library().fm_translation_set_centres(self._h, _ptr(o)))
+
+
+class RotationOptions(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("adam_eps", ctypes.c_double), ("cg_tol", ctypes.c_double), ("cg_max_iters", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
+def rotation_options(**kw) -> RotationOptions:
+    o = RotationOptions()
+    load_library().fm_rotation_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Rotation:
+    """Global rotation stage on the GPU (fm_rotation_*): column-wise initialisation by
+    conjugate gradients, then Adam on the geodesic objective in the 6D representation."""
+
+    def __init__(self, cam_i, cam_j, R_rel, n_cams: int, options: RotationOptions | None = None, stream=None):
+        lib = load_library()
+        ci = _host(cam_i, np.int32).reshape(-1)
+        cj = _host(cam_j, np.int32).reshape(-1)
+        Rr = _host(R_rel, np.float64).reshape(-1, 9)
+        self.n_cams, self.n_pairs = int(n_cams), ci.shape[0]
+        h = ctypes.c_void_p()
+        _check(lib.fm_rotation_create(self.n_cams, self.n_pairs, _ptr(ci), _ptr(cj), _ptr(Rr),
+                                      ctypes.byref(options) if options is not None else None,
+                                      stream if stream is not None else _current_stream(), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().fm_rotation_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def initialize(self):
+        """Column-wise initialisation; returns (conjugate-gradient iterations, relative residual)."""
+        it = ctypes.c_int32()
+        res = ctypes.c_double()
+        _check(load_library().fm_rotation_initialize(self._h, ctypes.byref(it), ctypes.byref(res)))
+        return it.value, res.value
+
+    def loss_grad(self):
+        loss = ctypes.c_double()
+        g = np.empty((self.n_cams, 6))
+        _check(load_library().fm_rotation_loss_grad(self._h, ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def step(self, n_iters: int = 1):
+        _check(load_library().fm_rotation_step(self._h, int(n_iters)))
+
+    def set_learning_rate(self, lr: float):
+        _check(load_library().fm_rotation_set_learning_rate(self._h, float(lr)))
+
+    def rotations(self) -> np.ndarray:
+        out = np.empty((self.n_cams, 3, 3))
+        _check(load_library().fm_rotation_get_rotations(self._h, _ptr(out)))
+        return out
+
+    def params(self) -> np.ndarray:
+        out = np.empty((self.n_cams, 6))
+        _check(load_library().fm_rotation_get_params(self._h, _ptr(out)))
+        return out
+
+    def set_rotations(self, R):
+        R = np.ascontiguousarray(_host(R, np.float64).reshape(self.n_cams, 9))
+        _check(load_library().fm_rotation_set_rotations(self._h, _ptr(R)))
+
+    def set_params(self, a6):
+        a6 = np.ascontiguousarray(_host(a6, np.float64).reshape(self.n_cams, 6))
+        _check(load_library().fm_rotation_set_params(self._h, _ptr(a6)))
 
 
 class Mlp:

@@ -501,3 +501,22 @@ def relative_translations(sc: Scene, noise_deg: float = 1.0, outlier_frac: float
     d[out] = _random_unit(int(out.sum()), g, torch.device("cpu"))
     d = d / torch.linalg.norm(d, dim=-1, keepdim=True)
     return d.numpy(), out.numpy()
+
+
+def relative_rotations(sc: Scene, noise_deg: float = 1.0, outlier_frac: float = 0.05, seed: int = 0):
+    """Relative rotations R_{i->j} = R_j R_i^T of the scene's image pairs from the true
+    rotations, each turned by a random rotation of about `noise_deg` degrees, and for a fraction
+    `outlier_frac` of the pairs turned by a uniformly random rotation angle instead.
+    Returns (R_rel (B, 3, 3) float64, outlier mask)."""
+    g = torch.Generator(device="cpu")
+    g.manual_seed(int(seed) * 104729 + 29)
+    R = sc.R_gt.detach().cpu().to(F64)
+    ci, cj = sc.cam_i.detach().cpu().long(), sc.cam_j.detach().cpu().long()
+    Rrel = R[cj] @ R[ci].transpose(1, 2)
+    B = Rrel.shape[0]
+    axis = _random_unit(B, g, torch.device("cpu"))
+    ang = math.radians(noise_deg) * torch.randn(B, 1, dtype=F64, generator=g)
+    out = torch.rand(B, dtype=F64, generator=g) < outlier_frac
+    ang[out, 0] = math.pi * torch.rand(int(out.sum()), dtype=F64, generator=g)
+    Rrel = rotation_exp(axis * ang) @ Rrel
+    return Rrel.numpy(), out.numpy()

@@ -49,7 +49,7 @@ def test_build_flags_target_sm_103a():
 
 
 def test_public_python_surface():
-    for name in ["Problem", "Mlp", "Translation", "Schedule", "refine", "epipolar_loss", "EpipolarLoss",
+    for name in ["Problem", "Mlp", "Translation", "Rotation", "Schedule", "refine", "epipolar_loss", "EpipolarLoss",
                  "default_options", "translation_options"]:
         assert hasattr(fm, name), name
     from paper_2605_18052_gb300 import learned, metrics, translation  # noqa: F401
@@ -103,3 +103,20 @@ def test_translation_rejects_bad_host_arguments_without_a_gpu(lib):
         assert ei.value.status == -1
     with pytest.raises(fm.FastMapError):
         fm.Translation(R, [0, 1], [1, 2], t, o, fm.translation_options(lr=0.0))
+
+
+def test_rotation_rejects_bad_host_arguments_without_a_gpu(lib):
+    I = np.eye(3)
+    Rz = np.array([[0.0, -1, 0], [1, 0, 0], [0, 0, 1]])
+    good = dict(cam_i=[0, 1], cam_j=[1, 2], R_rel=np.stack([I, Rz]), n=3)
+    cases = [
+        dict(good, cam_j=[1, 3]),                                  # index out of range
+        dict(good, cam_i=[0, 2], cam_j=[1, 2]),                    # cam_i == cam_j
+        dict(good, R_rel=np.stack([I, 2 * Rz])),                   # not orthonormal
+        dict(good, R_rel=np.stack([I, -Rz])),                      # det -1
+        dict(good, cam_i=[0], cam_j=[1], R_rel=I[None], n=3),      # camera 2 disconnected
+    ]
+    for c in cases:
+        with pytest.raises(fm.FastMapError) as ei:
+            fm.Rotation(c["cam_i"], c["cam_j"], c["R_rel"], c["n"])
+        assert ei.value.status == -1
