@@ -93,7 +93,7 @@ typedef struct {
     double beta1, beta2; /* Adam moment decay rates, in [0, 1) */
     double adam_eps;     /* Adam denominator epsilon, >= 0 */
     int32_t use_graph;   /* 1: replay captured CUDA graphs of chained iterations in fm_step */
-    int32_t reserved;    /* must be 0 */
+    int32_t refine_focal; /* 1: optimise each camera's focal length with the poses (0 or 1) */
     int64_t z_total;     /* Z of the objective; 0 means n_pp. A shard of a problem split across
                             processes sets the total point-pair count of all shards. */
 } fm_options;
@@ -210,6 +210,24 @@ FM_API fm_status fm_reset_optimizer(fm_problem *p);
  */
 FM_API fm_status fm_get_state(fm_problem *p, double *m, double *v, int64_t *step);
 FM_API fm_status fm_set_state(fm_problem *p, const double *m, const double *v, int64_t step);
+
+/* ---- focal refinement (last paragraph of Sec. "Epipolar Adjustment") ------------------------------
+ * The focal lengths can be optimised with the poses by building them into the pair matrices,
+ * which then are fundamental matrices. Keypoints are normalised with initial focal lengths f0_k;
+ * a refined f_k rescales camera k's normalised coordinates by s_k = f0_k / f_k, so
+ *   eps = x2^T F_n x1,  F_n = S_j E_n S_i,  S = diag(s, s, 1),
+ * and with opt.refine_focal = 1 every optimiser step (fm_step, fm_step_quadratic) also takes an
+ * Adam step on rho_k = log s_k (FP32 moments, FP64 rho; step size set below, default 1e-3).
+ * With refine_focal = 0 the scales stay as set (1 by default) and results are identical to the
+ * pose-only adjustment. fm_apply_gradient and fm_loss_grad_noalloc do not touch the scales.
+ */
+FM_API fm_status fm_set_focal_learning_rate(fm_problem *p, double lr);
+/* Per-camera scales s_k (host FP64 n_cams). Synchronises. */
+FM_API fm_status fm_get_focal_scales(fm_problem *p, double *s);
+/* Set the scales (host FP64 n_cams, > 0) and reset their Adam moments. Synchronises. */
+FM_API fm_status fm_set_focal_scales(fm_problem *p, const double *s);
+/* d loss / d rho_k (host FP64 n_cams) of the last fm_loss_grad or optimiser step. Synchronises. */
+FM_API fm_status fm_get_focal_gradient(fm_problem *p, double *g);
 
 /* ---- pre-aggregated quadratic form (Eq. epipolar-objective-l2 with the IRLS weights) ---------
  * With the weights held fixed, the objective of image pair n is quadratic in the 9 entries
@@ -418,7 +436,7 @@ FM_API fm_status fm_rotation_set_params(fm_rotation *rp, const double *a6);
  * Limits: 2 <= n_cams <= 4096, 1 <= n_pairs <= 32768, n_pairs <= n_pp <= 2^26; larger
  * problems return FM_EINVAL (use fm_create_problem for them).
  *
- * Intermediates live in one fixed 10.2 MiB __device__ array of the library, held on every
+ * Intermediates live in one fixed 10.7 MiB __device__ array of the library, held on every
  * device that loads it until the process exits. The first call on a device looks up the
  * array's device address with that device current; make that first call before any stream
  * capture. Every call shares the array, so calls that overlap on the GPU (other streams,

@@ -26,6 +26,7 @@ EXPORTED = [
     "fm_mlp_get_params", "fm_mlp_set_params", "fm_mlp_train_step", "fm_mlp_gradient", "fm_mlp_forward",
     "fm_set_scores", "fm_collect_features", "fm_learned_weights", "fm_reset_history",
     "fm_preaggregate", "fm_irls_preaggregate", "fm_loss_grad_quadratic", "fm_step_quadratic",
+    "fm_set_focal_learning_rate", "fm_get_focal_scales", "fm_set_focal_scales", "fm_get_focal_gradient",
     "fm_translation_default_options", "fm_translation_create", "fm_translation_destroy",
     "fm_translation_num_runs", "fm_translation_loss_grad", "fm_translation_step", "fm_translation_merge",
     "fm_translation_set_learning_rate", "fm_translation_get_centres", "fm_translation_set_centres",
@@ -45,7 +46,7 @@ class Options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("loss", ctypes.c_int32), ("delta", ctypes.c_double),
                 ("lr_rot", ctypes.c_double), ("lr_c", ctypes.c_double), ("beta1", ctypes.c_double),
                 ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32), ("z_total", ctypes.c_int64)]
+                ("use_graph", ctypes.c_int32), ("refine_focal", ctypes.c_int32), ("z_total", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -111,6 +112,10 @@ def load_library(path: str = LIB_PATH):
         "fm_irls_preaggregate": (I32, [P, D, P]),
         "fm_loss_grad_quadratic": (I32, [P, P, P]),
         "fm_step_quadratic": (I32, [P, I32]),
+        "fm_set_focal_learning_rate": (I32, [P, D]),
+        "fm_get_focal_scales": (I32, [P, P]),
+        "fm_set_focal_scales": (I32, [P, P]),
+        "fm_get_focal_gradient": (I32, [P, P]),
         "fm_translation_default_options": (None, [P]),
         "fm_translation_create": (I32, [I32, P, I32, P, P, P, I32, P, P, P, P]),
         "fm_translation_destroy": (None, [P]),
@@ -364,6 +369,24 @@ class Problem:
 
     def step(self, n_iters: int = 1):
         _check(load_library().fm_step(self._h, int(n_iters)))
+
+    # focal refinement (scales s_k = f0_k / f_k of the normalised keypoints)
+    def focal_scales(self) -> np.ndarray:
+        out = np.empty(self.n_cams)
+        _check(load_library().fm_get_focal_scales(self._h, _ptr(out)))
+        return out
+
+    def set_focal_scales(self, s):
+        s = np.ascontiguousarray(_host(s, np.float64).reshape(self.n_cams))
+        _check(load_library().fm_set_focal_scales(self._h, _ptr(s)))
+
+    def focal_gradient(self) -> np.ndarray:
+        out = np.empty(self.n_cams)
+        _check(load_library().fm_get_focal_gradient(self._h, _ptr(out)))
+        return out
+
+    def set_focal_learning_rate(self, lr: float):
+        _check(load_library().fm_set_focal_learning_rate(self._h, float(lr)))
 
     # pre-aggregated quadratic form of the IRLS objective (fixed weights)
     def preaggregate(self):

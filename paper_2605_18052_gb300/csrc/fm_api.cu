@@ -46,6 +46,7 @@ struct fm_problem {
     cudaGraphExec_t graph8 = nullptr;     // eight chained iterations
     bool timing = false;
     int hist_valid = 0;                   // d.le_hist holds a previous reweighting's residuals
+    double lr_focal = 1e-3;               // Adam step size of rho = log(f0/f)
     bool quad_alloc = false;              // d.qslots, d.quad, d.pair_rec allocated
     bool quad_valid = false;              // d.quad holds the form of the current weights
     cudaGraphExec_t qgraph = nullptr, qgraph8 = nullptr;  // quadratic-path iterations
@@ -132,7 +133,7 @@ fm_status upload_poses(fm_problem *p, const double *R, const double *t) {
 }
 
 fm_status upload_hyper(fm_problem *p) {
-    const double h[5] = {p->opt.lr_rot, p->opt.lr_c, p->opt.beta1, p->opt.beta2, p->opt.adam_eps};
+    const double h[6] = {p->opt.lr_rot, p->opt.lr_c, p->opt.beta1, p->opt.beta2, p->opt.adam_eps, p->lr_focal};
     FM_CUDA(cudaMemcpyAsync(p->d.hyper, h, sizeof h, cudaMemcpyHostToDevice, p->s));
     FM_CUDA(cudaStreamSynchronize(p->s));
     return FM_OK;
@@ -149,7 +150,7 @@ fm_status check_options(const fm_options *o) {
     if (!(o->beta1 >= 0.0 && o->beta1 < 1.0) || !(o->beta2 >= 0.0 && o->beta2 < 1.0))
         return fail(FM_EINVAL, "beta1 and beta2 must be in [0, 1)");
     if (!(o->adam_eps >= 0.0) || !std::isfinite(o->adam_eps)) return fail(FM_EINVAL, "adam_eps must be >= 0");
-    if (o->reserved != 0) return fail(FM_EINVAL, "reserved must be 0");
+    if (o->refine_focal != 0 && o->refine_focal != 1) return fail(FM_EINVAL, "refine_focal must be 0 or 1");
     if (o->z_total < 0) return fail(FM_EINVAL, "z_total must be >= 0");
     return FM_OK;
 }
@@ -266,6 +267,11 @@ fm_status create_impl(fm_problem *p, int32_t n_cams, const double *R, const doub
     FM_CUDA(dalloc(p, &d.c, 3 * (size_t)n_cams));
     FM_CUDA(dalloc(p, &d.m, 6 * (size_t)n_cams));
     FM_CUDA(dalloc(p, &d.v, 6 * (size_t)n_cams));
+    FM_CUDA(dalloc(p, &d.rho, (size_t)n_cams));
+    FM_CUDA(dalloc(p, &d.grad_rho, (size_t)n_cams));
+    FM_CUDA(dalloc(p, &d.rho_m, (size_t)n_cams));
+    FM_CUDA(dalloc(p, &d.rho_v, (size_t)n_cams));
+    d.refine_focal = p->opt.refine_focal;
     FM_CUDA(dalloc(p, &d.cam_loss, (size_t)camera_step_blocks(d)));
     FM_CUDA(dalloc(p, &d.hyper, 8));
     FM_CUDA(dalloc(p, &d.step, 1));
@@ -312,6 +318,10 @@ fm_status create_impl(fm_problem *p, int32_t n_cams, const double *R, const doub
     FM_CUDA(cudaMemsetAsync(d.err, 0, sizeof(unsigned), p->s));
     FM_CUDA(cudaMemsetAsync(d.m, 0, sizeof(float) * 6 * n_cams, p->s));
     FM_CUDA(cudaMemsetAsync(d.v, 0, sizeof(float) * 6 * n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(d.rho, 0, sizeof(double) * n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(d.grad_rho, 0, sizeof(double) * n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(d.rho_m, 0, sizeof(float) * n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(d.rho_v, 0, sizeof(float) * n_cams, p->s));
     FM_CUDA(cudaMemsetAsync(d.step, 0, sizeof(long long), p->s));
     FM_CUDA(cudaMemsetAsync(d.cen, 0, sizeof(float2) * n_cams, p->s));
     FM_CUDA(cudaMemsetAsync(d.geo, 0, sizeof(float) * GEO * n_pairs, p->s));
@@ -423,7 +433,7 @@ FM_API void fm_default_options(fm_options *o) {
     o->beta2 = 0.999;
     o->adam_eps = 1e-12;
     o->use_graph = 1;
-    o->reserved = 0;
+    o->refine_focal = 0;
     o->z_total = 0;
 }
 
@@ -798,6 +808,8 @@ FM_API fm_status fm_reset_optimizer(fm_problem *p) {
     FM_CUDA(join_in(p));
     FM_CUDA(cudaMemsetAsync(p->d.m, 0, sizeof(float) * 6 * p->d.n_cams, p->s));
     FM_CUDA(cudaMemsetAsync(p->d.v, 0, sizeof(float) * 6 * p->d.n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(p->d.rho_m, 0, sizeof(float) * p->d.n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(p->d.rho_v, 0, sizeof(float) * p->d.n_cams, p->s));
     FM_CUDA(cudaMemsetAsync(p->d.step, 0, sizeof(long long), p->s));
     FM_CUDA(cudaStreamSynchronize(p->s));
     return FM_OK;
@@ -843,6 +855,52 @@ FM_API fm_status fm_set_state(fm_problem *p, const double *m, const double *v, i
     FM_CUDA(cudaMemcpyAsync(p->d.step, &s, sizeof s, cudaMemcpyHostToDevice, p->s));
     FM_CUDA(cudaStreamSynchronize(p->s));
     return FM_OK;
+}
+
+// ---- focal refinement ----------------------------------------------------------------------------
+FM_API fm_status fm_set_focal_learning_rate(fm_problem *p, double lr) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!(lr >= 0.0) || !std::isfinite(lr)) return fail(FM_EINVAL, "lr must be finite and >= 0");
+    p->lr_focal = lr;
+    FM_CUDA(join_in(p));
+    return upload_hyper(p);
+}
+
+FM_API fm_status fm_get_focal_scales(fm_problem *p, double *s) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!s) return fail(FM_EINVAL, "s must not be NULL");
+    FM_CUDA(join_in(p));
+    FM_CUDA(cudaMemcpyAsync(s, p->d.rho, sizeof(double) * p->d.n_cams, cudaMemcpyDeviceToHost, p->s));
+    if (fm_status st = check_device_errors(p)) return st;
+    for (int k = 0; k < p->d.n_cams; ++k) s[k] = std::exp(s[k]);
+    return FM_OK;
+}
+
+FM_API fm_status fm_set_focal_scales(fm_problem *p, const double *s) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!s) return fail(FM_EINVAL, "s must not be NULL");
+    std::vector<double> rho(p->d.n_cams);
+    for (int k = 0; k < p->d.n_cams; ++k) {
+        if (!(s[k] > 0.0) || !std::isfinite(s[k])) return fail(FM_EINVAL, "scales must be finite and > 0");
+        rho[k] = std::log(s[k]);
+    }
+    FM_CUDA(join_in(p));
+    FM_CUDA(cudaMemcpyAsync(p->d.rho, rho.data(), sizeof(double) * p->d.n_cams, cudaMemcpyHostToDevice, p->s));
+    FM_CUDA(cudaMemsetAsync(p->d.rho_m, 0, sizeof(float) * p->d.n_cams, p->s));
+    FM_CUDA(cudaMemsetAsync(p->d.rho_v, 0, sizeof(float) * p->d.n_cams, p->s));
+    launch_cam_prep(p->d, p->s);
+    FM_CUDA(cudaGetLastError());
+    p->quad_valid = false;
+    FM_CUDA(cudaStreamSynchronize(p->s));
+    return FM_OK;
+}
+
+FM_API fm_status fm_get_focal_gradient(fm_problem *p, double *g) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!g) return fail(FM_EINVAL, "g must not be NULL");
+    FM_CUDA(join_in(p));
+    FM_CUDA(cudaMemcpyAsync(g, p->d.grad_rho, sizeof(double) * p->d.n_cams, cudaMemcpyDeviceToHost, p->s));
+    return check_device_errors(p);
 }
 
 // ---- pre-aggregated quadratic form ------------------------------------------------------------

@@ -21,7 +21,7 @@ namespace fm {
 constexpr int WR = 2048;           // point pairs per warp range
 constexpr int CTA_WARPS = 8;       // warps per CTA of the streaming kernels
 constexpr int SLOT = 12;           // floats per slot: G'(9), loss, 2 pad (48 B)
-constexpr int GEO = 36;            // floats per pair geometry record (144 B)
+constexpr int GEO = 40;            // floats per pair geometry record (160 B)
 constexpr int CAMREC = 16;         // floats per camera record
 constexpr int PG = 16;             // floats per pair gradient record
 constexpr float COORD_LIMIT = 8.0f;  // |normalized coordinate| bound (fixed-point centroids)
@@ -60,7 +60,12 @@ struct DevProblem {
     double z;               // Z of the objective (n_pp, or the total over all shards)
     float w_scale;          // FP16 weight scale s (1 for FP32 storage)
     // poses (FP64) and Adam moments (FP32)
-    double *R, *c, *hyper;   // hyper: lr_rot, lr_c, beta1, beta2, eps
+    double *R, *c, *hyper;   // hyper: lr_rot, lr_c, beta1, beta2, eps, lr_focal
+    // focal refinement: per camera rho = log(f0 / f), the scale of its normalised keypoints
+    // is exp(rho) (1 when rho is null); Adam moments of rho and its last gradient
+    double *rho, *grad_rho;
+    float *rho_m, *rho_v;
+    int refine_focal;
     float *m, *v;
     long long *step;
     double *cam_loss;        // per-block loss partials of the fused step kernel

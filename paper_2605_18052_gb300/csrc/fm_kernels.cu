@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(CTA_WARPS * 32) k_residuals(DevProblem d, floa
 __global__ void k_cam_prep(DevProblem d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n_cams) return;
-    write_camrec(d.cam + (size_t)k * CAMREC, d.R + 9 * (size_t)k, d.c + 3 * (size_t)k);
+    write_camrec(d.cam + (size_t)k * CAMREC, d.R + 9 * (size_t)k, d.c + 3 * (size_t)k, camera_scale(d, k));
 }
 
 // prev_blocks > 0: this pass follows an optimiser step whose camera-step kernel had that many
@@ -324,12 +324,12 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather(DevProblem d, int cou
 // next kernel (pair setup or the finalize kernel) adds them up and advances the step count.
 __global__ void __launch_bounds__(STEP_CAMS * 32, 4)
 k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
-    __shared__ float s_hi[7][STEP_CAMS], s_lo[7][STEP_CAMS];
+    __shared__ float s_hi[STEP_VALS][STEP_CAMS], s_lo[STEP_VALS][STEP_CAMS];
     __shared__ int4 s_item[STEP_CAMS][32];
     __shared__ __align__(16) float s_geo[STEP_CAMS][32][GEO];
     __shared__ float s_mv[STEP_CAMS][12];     // Adam m (6) and v (6) of the block's cameras
     __shared__ double s_Rc[STEP_CAMS][12];    // R (9) and c (3) of the block's cameras
-    __shared__ double s_hyper[5];
+    __shared__ double s_hyper[6];   // lr_rot, lr_c, beta1, beta2, eps, lr_focal
     __shared__ double s_loss[STEP_CAMS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = blockIdx.x * STEP_CAMS + warp;
@@ -342,7 +342,7 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
                 s_Rc[cc][q] = q < 9 ? d.R[(size_t)(cam0 + cc) * 9 + q] : d.c[(size_t)(cam0 + cc) * 3 + q - 9];
             }
         }
-        if (threadIdx.x < 5) s_hyper[threadIdx.x] = d.hyper[threadIdx.x];
+        if (threadIdx.x < 6) s_hyper[threadIdx.x] = d.hyper[threadIdx.x];
     }
     const int e_begin = k < d.n_cams ? d.cam_off[k] : 0;
     const int e_end = k < d.n_cams ? d.cam_off[k + 1] : 0;
@@ -377,9 +377,9 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
     pdl_trigger();
     const long long t_step = *d.step + 1;
     if (k < d.n_cams) {
-        float hi[7], lo[7];
+        float hi[STEP_VALS], lo[STEP_VALS];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) hi[q] = lo[q] = 0.f;
+        for (int q = 0; q < STEP_VALS; ++q) hi[q] = lo[q] = 0.f;
         for (int base = e_begin; base < e_end; base += 32) {
             if (base != e_begin) {
                 __syncwarp();
@@ -396,16 +396,16 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
                 const float4 *sl = reinterpret_cast<const float4 *>(d.slots + (size_t)(it.y + it.w + (t - it.x)) * SLOT);
                 const float4 sa = sl[0], sb = sl[1], sc = sl[2];
                 const float sum[10] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w, sc.x, sc.y};
-                float contrib[7];
+                float contrib[STEP_VALS];
                 pair_chain_rule(s_geo[warp][lo_i], it.z, sum, gscale, lscale, contrib);
 #pragma unroll
-                for (int q = 0; q < 7; ++q) two_sum_acc(hi[q], lo[q], contrib[q], 0.f);
+                for (int q = 0; q < STEP_VALS; ++q) two_sum_acc(hi[q], lo[q], contrib[q], 0.f);
             }
         }
-        warp_two_sum_reduce<7>(hi, lo);
+        warp_two_sum_reduce<STEP_VALS>(hi, lo);
         if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < 7; ++q) {
+            for (int q = 0; q < STEP_VALS; ++q) {
                 s_hi[q][warp] = hi[q];
                 s_lo[q][warp] = lo[q];
             }
@@ -471,7 +471,7 @@ __global__ void k_apply_gradient(DevProblem d) {
         for (int q = 0; q < 9; ++q) d.R[(size_t)kc * 9 + q] = Rn[q];
 #pragma unroll
         for (int q = 0; q < 3; ++q) d.c[(size_t)kc * 3 + q] = cn[q];
-        write_camrec(d.cam + (size_t)kc * CAMREC, Rn, cn);
+        write_camrec(d.cam + (size_t)kc * CAMREC, Rn, cn, camera_scale(d, kc));
     }
 }
 

@@ -34,7 +34,7 @@ constexpr size_t OFF_PG = OFF_SLOTS + al256(sizeof(float) * SLOT * ((size_t)NA_M
 constexpr size_t OFF_CAMOFF = OFF_PG + al256(sizeof(float) * PG * NA_MAX_PAIRS);
 constexpr size_t OFF_CAMENT = OFF_CAMOFF + al256(sizeof(int) * (NA_MAX_CAMS + 1));
 constexpr size_t OFF_ERR = OFF_CAMENT + al256(sizeof(int) * 2 * NA_MAX_PAIRS);
-constexpr size_t NA_SCRATCH_BYTES = OFF_ERR + 256;   // about 10.2 MiB
+constexpr size_t NA_SCRATCH_BYTES = OFF_ERR + 256;   // about 10.7 MiB
 
 // Host code must not use this name as an address: it is a host-side stand-in. The device
 // address comes from cudaGetSymbolAddress (scratch_base below).

@@ -155,10 +155,10 @@ __global__ void k_quad_combine(DevProblem d) {
 // the chain's length to *d.step.
 __global__ void __launch_bounds__(STEP_CAMS * 32, 4)
 k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gscale, float lscale, int apply) {
-    __shared__ float s_hi[7][STEP_CAMS], s_lo[7][STEP_CAMS];
+    __shared__ float s_hi[STEP_VALS][STEP_CAMS], s_lo[STEP_VALS][STEP_CAMS];
     __shared__ float s_mv[STEP_CAMS][12];
     __shared__ double s_Rc[STEP_CAMS][12];
-    __shared__ double s_hyper[5];
+    __shared__ double s_hyper[6];   // lr_rot, lr_c, beta1, beta2, eps, lr_focal
     __shared__ double s_loss[STEP_CAMS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = blockIdx.x * STEP_CAMS + warp;
@@ -187,13 +187,13 @@ k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gs
                 s_Rc[cc][q] = q < 9 ? d.R[(size_t)(cam0 + cc) * 9 + q] : d.c[(size_t)(cam0 + cc) * 3 + q - 9];
             }
         }
-        if (threadIdx.x < 5) s_hyper[threadIdx.x] = d.hyper[threadIdx.x];
+        if (threadIdx.x < 6) s_hyper[threadIdx.x] = d.hyper[threadIdx.x];
     }
     const long long t_step = *d.step + 1 + it;
     if (k < d.n_cams) {
-        float hi[7], lo[7];
+        float hi[STEP_VALS], lo[STEP_VALS];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) hi[q] = lo[q] = 0.f;
+        for (int q = 0; q < STEP_VALS; ++q) hi[q] = lo[q] = 0.f;
         for (; e < e_end; e += 32) {
             if (e >= e_begin + 32) {
                 const int ent = d.cam_ent[e];
@@ -243,15 +243,15 @@ k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gs
 #pragma unroll
             for (int a = 0; a < 9; ++a) loss = fmaf(dv[a], q[a], loss);
             const float sum[10] = {q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8], loss};
-            float contrib[7];
+            float contrib[STEP_VALS];
             pair_chain_rule(g, role, sum, gscale, lscale, contrib);
 #pragma unroll
-            for (int w = 0; w < 7; ++w) two_sum_acc(hi[w], lo[w], contrib[w], 0.f);
+            for (int w = 0; w < STEP_VALS; ++w) two_sum_acc(hi[w], lo[w], contrib[w], 0.f);
         }
-        warp_two_sum_reduce<7>(hi, lo);
+        warp_two_sum_reduce<STEP_VALS>(hi, lo);
         if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < 7; ++q) {
+            for (int q = 0; q < STEP_VALS; ++q) {
                 s_hi[q][warp] = hi[q];
                 s_lo[q][warp] = lo[q];
             }

@@ -10,6 +10,7 @@
 namespace fm {
 
 constexpr int STEP_CAMS = 8;   // cameras (warps) per block of the step kernels
+constexpr int STEP_VALS = 8;   // per camera: 6 pose gradient components, loss, scale gradient
 
 // (hi, lo) += (bhi, blo) with the rounding error of the high parts kept (Knuth's TwoSum)
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float bhi, float blo) {
@@ -22,7 +23,8 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float bhi, flo
 }
 
 // ---- per camera: pose record --------------------------------------------------------------------
-__device__ __forceinline__ void write_camrec(float *rec, const double *R, const double *c) {
+// R (9 floats), centre as hi + lo floats (3 + 3), keypoint scale s (focal refinement)
+__device__ __forceinline__ void write_camrec(float *rec, const double *R, const double *c, double s) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) rec[i] = (float)R[i];
 #pragma unroll
@@ -31,7 +33,12 @@ __device__ __forceinline__ void write_camrec(float *rec, const double *R, const 
         rec[9 + q] = hi;
         rec[12 + q] = (float)(c[q] - (double)hi);
     }
-    rec[15] = 0.f;
+    rec[15] = (float)s;
+}
+
+// keypoint scale of camera k: exp(rho_k), 1 without focal state
+__device__ __forceinline__ double camera_scale(const DevProblem &d, int k) {
+    return d.rho ? exp(d.rho[k]) : 1.0;
 }
 
 __device__ __forceinline__ void vee(const float *M, float *v) {
@@ -91,8 +98,10 @@ __device__ __forceinline__ void orthonormalize_rows(double *R) {
 
 // Chain rule of one image pair (or one range partial of it) to one of its cameras.
 // gr = the pair's geometry record, sum[0..8] = sum s * o2 o1^T over the point pairs,
-// sum[9] = their loss terms. Writes the camera's 6 gradient components and (for the first
-// camera only) the loss.
+// sum[9] = their loss terms. Writes the camera's 6 pose gradient components, (for the first
+// camera only) the loss in contrib[6], and in contrib[7] the gradient with respect to the
+// camera's keypoint scale s: with F = S_j E S_i, dL/dE = S_j G S_i (G = dL/dF) and
+// dL/ds_i = sum_{a, b<2} G_ab E_ab (S_j)_a, dL/ds_j = sum_{a<2, b} G_ab E_ab (S_i)_b.
 __device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const float *sum,
                                                 float gscale, float lscale, float *contrib) {
     float Gp[9];
@@ -117,6 +126,31 @@ __device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const
     const float inv = gr[21];
     const float *Rj = gr + 24;
     const float th[3] = {tn[0] * inv, tn[1] * inv, tn[2] * inv};
+    // focal: E = [th]_x R_n, the scale gradient from G = dL/dF, then G <- dL/dE
+    const float s_i = gr[35], s_j = gr[36];
+    {
+        float E[9];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            E[b] = -th[2] * Rn[3 + b] + th[1] * Rn[6 + b];
+            E[3 + b] = th[2] * Rn[b] - th[0] * Rn[6 + b];
+            E[6 + b] = -th[1] * Rn[b] + th[0] * Rn[3 + b];
+        }
+        const float si[3] = {s_i, s_i, 1.f}, sj[3] = {s_j, s_j, 1.f};
+        float gs = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const float ge = G[3 * a + b] * E[3 * a + b];
+                if (role == 0 ? b < 2 : a < 2) gs = fmaf(ge, role == 0 ? sj[a] : si[b], gs);
+            }
+        contrib[7] = gs;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) G[3 * a + b] = (G[3 * a + b] * sj[a]) * si[b];
+    }
     float A[9];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -183,9 +217,10 @@ __device__ __forceinline__ void warp_two_sum_reduce(float *hi, float *lo) {
 // Phase 2 of a step for camera kc, one lane: the FP64 sum of the gradient's hi + lo parts, then
 // either the gradient is written (apply = 0) or one Adam step (FP32 moments) with the FP64
 // exponential map, re-orthonormalisation and centre update, and the new camera record at
-// rec_out. hi/lo hold 7 values (6 gradient components, the loss) `stride` apart; mv = the
-// camera's Adam m (6) and v (6); Rc = its R (9) and c (3); hyper = lr_rot, lr_c, beta1, beta2,
-// eps. Returns the camera's loss share.
+// rec_out. hi/lo hold STEP_VALS values (6 pose gradient components, the loss, the keypoint-
+// scale gradient) `stride` apart; mv = the camera's Adam m (6) and v (6); Rc = its R (9) and
+// c (3); hyper = lr_rot, lr_c, beta1, beta2, eps, lr_focal. With focal refinement rho = log s
+// takes its own Adam step (gradient s dL/ds). Returns the camera's loss share.
 __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, const float *hi, const float *lo,
                                                 int stride, const float *mv, const double *Rc,
                                                 const double *hyper, long long t_step, int apply,
@@ -199,14 +234,29 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
     }
     if (!ok) atomicOr(d.err, ERR_NONFINITE);
     const double bl = (double)hi[6 * stride] + (double)lo[6 * stride];
+    const double s_cur = camera_scale(d, kc);
+    const double g_rho = s_cur * ((double)hi[7 * stride] + (double)lo[7 * stride]);
     if (!apply) {
 #pragma unroll
         for (int q = 0; q < 6; ++q) d.grad[(size_t)kc * 6 + q] = g[q];
+        if (d.grad_rho) d.grad_rho[kc] = g_rho;
         return bl;
     }
+    double s_new = s_cur;
     const float b1 = (float)hyper[2], b2 = (float)hyper[3], eps = (float)hyper[4];
     const float lr_r = (float)hyper[0], lr_c = (float)hyper[1];
     const float bc1 = 1.f - powf(b1, (float)t_step), bc2 = 1.f - powf(b2, (float)t_step);
+    if (d.refine_focal) {
+        const float gq = (float)g_rho;
+        const float mo = b1 * d.rho_m[kc] + (1.f - b1) * gq;
+        const float vo = b2 * d.rho_v[kc] + (1.f - b2) * gq * gq;
+        d.rho_m[kc] = mo;
+        d.rho_v[kc] = vo;
+        const double r = d.rho[kc] - (double)((float)hyper[5] * (mo / bc1) / (sqrtf(vo / bc2) + eps));
+        d.rho[kc] = r;
+        d.grad_rho[kc] = g_rho;
+        s_new = exp(r);
+    }
     double dl[6];
     float mo[6], vo[6];
 #pragma unroll
@@ -237,7 +287,7 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
     for (int q = 0; q < 9; ++q) d.R[(size_t)kc * 9 + q] = Rn[q];
 #pragma unroll
     for (int q = 0; q < 3; ++q) d.c[(size_t)kc * 3 + q] = cn[q];
-    write_camrec(rec_out, Rn, cn);
+    write_camrec(rec_out, Rn, cn, s_new);
     return bl;
 }
 

@@ -198,7 +198,8 @@ __device__ __forceinline__ void walk_range(const DevProblem &d, int r, int lane,
 }
 
 // ---- per pair: relative pose and folded essential matrix ------------------------------------------
-__device__ __forceinline__ void load_camrec(const float *rec, float *R, float *hi, float *lo) {
+// camera record: R (9), centre as hi (3) + lo (3) floats, s = scale of the normalised keypoints
+__device__ __forceinline__ void load_camrec(const float *rec, float *R, float *hi, float *lo, float &s) {
     const float4 *v = reinterpret_cast<const float4 *>(rec);
     const float4 a = v[0], b = v[1], c = v[2], e = v[3];
     R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w;
@@ -206,17 +207,21 @@ __device__ __forceinline__ void load_camrec(const float *rec, float *R, float *h
     R[8] = c.x;
     hi[0] = c.y; hi[1] = c.z; hi[2] = c.w;
     lo[0] = e.x; lo[1] = e.y; lo[2] = e.z;
+    s = e.w;
 }
 
 
-// Relative pose and centroid-folded essential matrix of the pair (i, j) from the camera
-// records `cam` into the geometry record g (registers): E'_n = T_j^T [t_n/|t_n|]_x R_n T_i,
-// R_n = R_j R_i^T, t_n = R_j (c_i - c_j). Returns false (and g with 1/|t_n| = 0) when the
-// baseline is degenerate.
+// Relative pose and centroid-folded matrix of the pair (i, j) from the camera records `cam`
+// into the geometry record g (registers): E'_n = T_j^T S_j [t_n/|t_n|]_x R_n S_i T_i,
+// R_n = R_j R_i^T, t_n = R_j (c_i - c_j), S = diag(s, s, 1) the cameras' keypoint scales
+// (focal refinement; 1 otherwise, which leaves the essential matrix unchanged). Returns false
+// (and g with 1/|t_n| = 0) when the baseline is degenerate.
+// Record: 0..8 E', 9..17 R_n, 18..20 t_n, 21 1/|t_n|, 22..23 centroid i, 24..32 R_j,
+// 33..34 centroid j, 35 s_i, 36 s_j, 37..39 0.
 __device__ __forceinline__ bool pair_geometry_regs(const float *cam, const float2 *cen, int i, int j, float *g) {
-    float Ri[9], Rj[9], hi_i[3], lo_i[3], hi_j[3], lo_j[3], dc[3];
-    load_camrec(cam + (size_t)i * CAMREC, Ri, hi_i, lo_i);
-    load_camrec(cam + (size_t)j * CAMREC, Rj, hi_j, lo_j);
+    float Ri[9], Rj[9], hi_i[3], lo_i[3], hi_j[3], lo_j[3], dc[3], s_i, s_j;
+    load_camrec(cam + (size_t)i * CAMREC, Ri, hi_i, lo_i, s_i);
+    load_camrec(cam + (size_t)j * CAMREC, Rj, hi_j, lo_j, s_j);
     // c_i - c_j from the two-float representation: the high parts of nearby centres
     // subtract exactly, so the baseline keeps FP32 relative accuracy far from the origin
 #pragma unroll
@@ -239,13 +244,20 @@ __device__ __forceinline__ bool pair_geometry_regs(const float *cam, const float
     const bool ok = nt2 > floor2 && isfinite(nt2);
     const float inv = ok ? 1.0f / sqrtf(nt2) : 0.f;
     const float th[3] = {tn[0] * inv, tn[1] * inv, tn[2] * inv};
-    // E = [th]_x R_n
+    // E = [th]_x R_n, then F = S_j E S_i
     float E[9];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
         E[b] = -th[2] * Rn[3 + b] + th[1] * Rn[6 + b];
         E[3 + b] = th[2] * Rn[b] - th[0] * Rn[6 + b];
         E[6 + b] = -th[1] * Rn[b] + th[0] * Rn[3 + b];
+    }
+    {
+        const float si[3] = {s_i, s_i, 1.f}, sj[3] = {s_j, s_j, 1.f};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) E[3 * a + b] = (E[3 * a + b] * sj[a]) * si[b];
     }
     // E' = T_j^T E T_i with T = [[1,0,cx],[0,1,cy],[0,0,1]] (keypoints stored as offsets o = x - c)
     const float2 cen_i = cen[i], cen_j = cen[j];
@@ -271,7 +283,9 @@ __device__ __forceinline__ bool pair_geometry_regs(const float *cam, const float
     for (int k = 0; k < 9; ++k) g[24 + k] = Rj[k];
     g[33] = cen_j.x;
     g[34] = cen_j.y;
-    g[35] = 0.f;
+    g[35] = s_i;
+    g[36] = s_j;
+    g[37] = g[38] = g[39] = 0.f;
     return ok;
 }
 

@@ -84,6 +84,8 @@ class Scene:
 #   traj1000  : 1,000 cameras along a smooth random trajectory, 500k points, 20 neighbours
 #               (~1e4 pairs), log-normal counts (~5e7 point pairs), 20% outliers, 1 px.
 #   traj1000_o30 : traj1000 with 30% outliers (learned-weight evaluation scene).
+#   sphere128_o30 : sphere128 with 30% outliers (the learned weights' training distribution;
+#               evaluated on seeds outside the training seeds 1000-1199).
 #   traj4000  : 4,000 cameras, 2M points, 25 neighbours (~5e4 pairs), Pareto(1.5) counts
 #               capped at 50k (~1.5e8 point pairs), 25% outliers, 1.5 px.
 CONFIGS = {
@@ -91,6 +93,8 @@ CONFIGS = {
                    keep=0.5, iters=200),
     "sphere128": dict(kind="sphere", n_cams=128, n_pts=50_000, sigma_px=1.0, outlier=0.15,
                       knn=16, counts=("lognormal", 2000.0, 0.9, 20_000), iters=300),
+    "sphere128_o30": dict(kind="sphere", n_cams=128, n_pts=50_000, sigma_px=1.0, outlier=0.30,
+                          knn=16, counts=("lognormal", 2000.0, 0.9, 20_000), iters=300),
     "traj1000": dict(kind="trajectory", n_cams=1000, n_pts=500_000, sigma_px=1.0,
                      outlier=0.20, knn=20, counts=("lognormal", 3900.0, 0.9, 20_000),
                      spacing=0.25, depth=(3.0, 9.0), iters=300),
