@@ -186,6 +186,16 @@ FM_API fm_status fm_residuals(fm_problem *p, float *eps);
  */
 FM_API fm_status fm_step(fm_problem *p, int32_t n_iters);
 
+/*
+ * One IRLS round: fm_irls_weights(tau) followed by fm_step(n_iters), with the reweighting fused
+ * into the first iteration's pass over the point pairs (the weights come from the residuals at
+ * the round's starting poses, which that pass computes anyway): the same arithmetic, bit for
+ * bit, and one read of the keypoints less. n_iters >= 1; IRLS objective only. Writes the
+ * number of kept point pairs to *n_active if it is not NULL (then synchronises; otherwise
+ * only enqueues work).
+ */
+FM_API fm_status fm_step_irls(fm_problem *p, double tau, int32_t n_iters, int64_t *n_active);
+
 /* Objective value of the most recent iteration of fm_step (or fm_loss_grad). Synchronises. */
 FM_API fm_status fm_last_loss(fm_problem *p, double *loss);
 

@@ -19,7 +19,7 @@ FM_LOSS_IRLS, FM_LOSS_L1 = 0, 1
 EXPORTED = [
     "fm_default_options", "fm_create_problem", "fm_destroy_problem", "fm_problem_info",
     "fm_get_poses", "fm_set_poses", "fm_get_params", "fm_set_params", "fm_set_params_device", "fm_set_weights", "fm_get_weights", "fm_irls_weights",
-    "fm_loss_grad", "fm_loss_grad_device", "fm_residuals", "fm_step", "fm_last_loss",
+    "fm_loss_grad", "fm_loss_grad_device", "fm_residuals", "fm_step", "fm_step_irls", "fm_last_loss",
     "fm_set_learning_rate", "fm_reset_optimizer", "fm_get_state", "fm_set_state",
     "fm_synchronize", "fm_apply_gradient", "fm_enable_kernel_timing", "fm_kernel_time", "fm_loss_grad_noalloc",
     "fm_status_string", "fm_last_error", "fm_mlp_num_params", "fm_mlp_create", "fm_mlp_destroy",
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "fm_loss_grad_device": (I32, [P, P, P]),
         "fm_residuals": (I32, [P, P]),
         "fm_step": (I32, [P, I32]),
+        "fm_step_irls": (I32, [P, D, I32, P]),
         "fm_last_loss": (I32, [P, P]),
         "fm_set_learning_rate": (I32, [P, D, D]),
         "fm_reset_optimizer": (I32, [P]),
@@ -369,6 +370,13 @@ class Problem:
 
     def step(self, n_iters: int = 1):
         _check(load_library().fm_step(self._h, int(n_iters)))
+
+    def step_irls(self, tau: float, n_iters: int, count: bool = False):
+        """One IRLS round: reweighting at threshold tau fused into the first of n_iters
+        iterations. Returns the number of kept point pairs if `count` (synchronises)."""
+        n = ctypes.c_int64()
+        _check(load_library().fm_step_irls(self._h, float(tau), int(n_iters), ctypes.byref(n) if count else None))
+        return n.value if count else None
 
     # focal refinement (scales s_k = f0_k / f_k of the normalised keypoints)
     def focal_scales(self) -> np.ndarray:

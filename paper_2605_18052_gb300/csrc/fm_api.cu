@@ -50,6 +50,7 @@ struct fm_problem {
     bool quad_alloc = false;              // d.qslots, d.quad, d.pair_rec allocated
     bool quad_valid = false;              // d.quad holds the form of the current weights
     cudaGraphExec_t qgraph = nullptr, qgraph8 = nullptr;  // quadratic-path iterations
+    cudaGraphExec_t rgraph = nullptr;     // one iteration whose pass is fused with the reweighting
     std::vector<cudaEvent_t> tev;   // timing events, pairs (start, end)
     size_t tev_used = 0;
     int input_was_sorted = 0;
@@ -157,8 +158,13 @@ fm_status check_options(const fm_options *o) {
 
 // one optimiser iteration (three launches, chained with programmatic dependent launch);
 // `first` = the iteration does not follow another one in this chain
-void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed, bool first) {
+void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed, bool first, bool reweight = false) {
     launch_pair_setup(p->d, s, true, !first);
+    if (reweight) {   // the round's reweighting fused into this pass (not part of kernel timing)
+        launch_stream_reweight(p->d, s, true);
+        launch_camera_step(p->d, true, s, true);
+        return;
+    }
     if (timed) {
         if (p->tev_used + 2 > p->tev.size()) {
             for (int k = 0; k < 64; ++k) {
@@ -195,11 +201,16 @@ void enqueue_iterations(fm_problem *p, cudaStream_t s, bool timed, int iters, bo
     launch_finalize(p->d, true, s, !timed);
 }
 
-// a graph of `iters` chained iterations
-fm_status build_graph(fm_problem *p, int iters, cudaGraphExec_t *out, bool quad = false) {
+// a graph of `iters` chained iterations (reweight: one iteration fused with the reweighting)
+fm_status build_graph(fm_problem *p, int iters, cudaGraphExec_t *out, bool quad = false, bool reweight = false) {
     cudaGraph_t g = nullptr;
     FM_CUDA(cudaStreamBeginCapture(p->s, cudaStreamCaptureModeThreadLocal));
-    enqueue_iterations(p, p->s, false, iters, quad);
+    if (reweight) {
+        enqueue_iteration(p, p->s, false, true, true);
+        launch_finalize(p->d, true, p->s, true);
+    } else {
+        enqueue_iterations(p, p->s, false, iters, quad);
+    }
     cudaError_t e = cudaStreamEndCapture(p->s, &g);
     if (e != cudaSuccess) return fail(FM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(out, g, 0);
@@ -219,6 +230,7 @@ void free_problem(fm_problem *p) {
     if (p->graph8) cudaGraphExecDestroy(p->graph8);
     if (p->qgraph) cudaGraphExecDestroy(p->qgraph);
     if (p->qgraph8) cudaGraphExecDestroy(p->qgraph8);
+    if (p->rgraph) cudaGraphExecDestroy(p->rgraph);
     for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
@@ -765,6 +777,39 @@ FM_API fm_status fm_step(fm_problem *p, int32_t n_iters) {
         int left = n_iters;
         for (; left >= 8; left -= 8) FM_CUDA(cudaGraphLaunch(p->graph8, p->s));
         for (; left > 0; --left) FM_CUDA(cudaGraphLaunch(p->graph, p->s));
+    }
+    FM_CUDA(join_out(p));
+    return FM_OK;
+}
+
+FM_API fm_status fm_step_irls(fm_problem *p, double tau, int32_t n_iters, int64_t *n_active) {
+    if (fm_status st = check_problem(p)) return st;
+    if (std::isnan(tau) || tau < 0.0) return fail(FM_EINVAL, "tau must be >= 0 (may be +inf)");
+    if (n_iters < 1) return fail(FM_EINVAL, "n_iters must be >= 1");
+    if (p->d.loss != FM_LOSS_IRLS) return fail(FM_EINVAL, "the fused reweighting needs the IRLS objective");
+    FM_CUDA(join_in(p));
+    const double tv = std::isinf(tau) ? INFINITY : (double)(float)tau;
+    FM_CUDA(cudaMemcpyAsync(p->d.hyper + 6, &tv, sizeof tv, cudaMemcpyHostToDevice, p->s));
+    FM_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(unsigned long long), p->s));
+    p->quad_valid = false;
+    if (p->timing || !p->opt.use_graph) {
+        enqueue_iteration(p, p->s, false, true, true);
+        launch_finalize(p->d, true, p->s, true);
+        FM_CUDA(cudaGetLastError());
+    } else {
+        if (!p->rgraph) {
+            fm_status st = build_graph(p, 1, &p->rgraph, false, true);
+            if (st != FM_OK) return st;
+        }
+        FM_CUDA(cudaGraphLaunch(p->rgraph, p->s));
+    }
+    unsigned long long cnt = 0;
+    if (n_active) FM_CUDA(cudaMemcpyAsync(&cnt, p->d.counter, sizeof cnt, cudaMemcpyDeviceToHost, p->s));
+    if (n_iters > 1)
+        if (fm_status st = fm_step(p, n_iters - 1)) return st;
+    if (n_active) {
+        if (fm_status st = check_device_errors(p)) return st;
+        *n_active = (int64_t)cnt;
     }
     FM_CUDA(join_out(p));
     return FM_OK;

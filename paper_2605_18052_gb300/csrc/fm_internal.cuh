@@ -60,7 +60,7 @@ struct DevProblem {
     double z;               // Z of the objective (n_pp, or the total over all shards)
     float w_scale;          // FP16 weight scale s (1 for FP32 storage)
     // poses (FP64) and Adam moments (FP32)
-    double *R, *c, *hyper;   // hyper: lr_rot, lr_c, beta1, beta2, eps, lr_focal
+    double *R, *c, *hyper;   // hyper: lr_rot, lr_c, beta1, beta2, eps, lr_focal, tau (fused reweighting)
     // focal refinement: per camera rho = log(f0 / f), the scale of its normalised keypoints
     // is exp(rho) (1 when rho is null); Adam moments of rho and its last gradient
     double *rho, *grad_rho;
@@ -141,6 +141,8 @@ int camera_step_blocks(const DevProblem &d);
 void loss_scales(const DevProblem &d, float &gscale, float &lscale);
 // streaming loss + adjoint: per (image pair, CTA range) partial sums in d.slots
 void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl = false);
+// the same pass fused with the IRLS reweighting at threshold d.hyper[6]; kept count in d.counter
+void launch_stream_reweight(const DevProblem &d, cudaStream_t s, bool pdl = false);
 void launch_combine(const DevProblem &d, cudaStream_t s);
 void launch_gather(const DevProblem &d, bool count_step, cudaStream_t s);
 // fused per-camera step: combine this camera's pair partials, chain rule, FP64 sum, Adam,

@@ -80,6 +80,70 @@ __global__ void __launch_bounds__(CTA_WARPS * 32, 4) k_stream_loss(DevProblem d)
     walk_range<STORE, MODE == MODE_LOSS_IRLS>(d, r, threadIdx.x & 31, body);
 }
 
+// The first pass of an IRLS round fused with the round's reweighting: the residual at the
+// round's starting poses gives the weight (filtered by tau, floored by delta, quantised as the
+// storage keeps it), which is written and at once used for the loss and adjoint sums. Same
+// arithmetic as the weights kernel followed by the streaming pass, one read of the keypoints
+// instead of two. tau comes from d.hyper[6] so one captured graph serves every round.
+template <int STORE>
+struct ReweightLossBody {
+    LossBody<MODE_LOSS_IRLS> loss;
+    const DevProblem &d;
+    float tau, delta, scale;
+    float out[2];
+    unsigned kept;
+    __device__ ReweightLossBody(const DevProblem &dd, float t)
+        : loss(dd), d(dd), tau(t), delta((float)dd.delta), scale(dd.w_scale), kept(0) {
+        out[0] = out[1] = 0.f;
+    }
+    __device__ __forceinline__ void point(int k, float e, float x1, float y1, float x2, float y2, float) {
+        const float a = fabsf(e);
+        const bool keep = a <= tau;  // NaN residuals are filtered
+        const float wf = keep ? 1.0f / fmaxf(a, delta) : 0.f;
+        const float w = STORE == FM_STORE_FP32 ? wf : __half2float(__float2half_rn(wf * scale));
+        out[k] = w;
+        kept += keep ? 1u : 0u;
+        loss.point(k, e, x1, y1, x2, y2, w);
+    }
+    __device__ __forceinline__ void segment_begin(int seg) { loss.segment_begin(seg); }
+    __device__ __forceinline__ void segment_end(int seg, int r, int lane, bool last) {
+        loss.segment_end(seg, r, lane, last);
+    }
+    __device__ __forceinline__ void group_done(int64_t gb, int64_t p_end, int lane) {
+        const int64_t q = gb + lane * Fmt<STORE>::PPL;
+        if (STORE == FM_STORE_FP32) {
+            static_cast<float *>(d.w)[q] = q < p_end ? out[0] : 0.f;
+        } else {
+            // already on the FP16 grid: the conversion is exact
+            const float a = q < p_end ? out[0] : 0.f;
+            const float b = q + 1 < p_end ? out[1] : 0.f;
+            reinterpret_cast<__half2 *>(d.w)[q >> 1] = __floats2half2_rn(a, b);
+        }
+        out[0] = out[1] = 0.f;
+    }
+};
+
+template <int STORE>
+__global__ void __launch_bounds__(CTA_WARPS * 32, 4) k_stream_reweight(DevProblem d) {
+    __shared__ unsigned cta_kept;
+    if (threadIdx.x == 0) cta_kept = 0;
+    __syncthreads();
+    pdl_wait();     // pair geometry of this pass
+    pdl_trigger();
+    const float tau = (float)d.hyper[6];
+    const int r = blockIdx.x * CTA_WARPS + (threadIdx.x >> 5);
+    if (r < d.n_ranges) {
+        ReweightLossBody<STORE> body(d, tau);
+        walk_range<STORE, false>(d, r, threadIdx.x & 31, body);
+        unsigned k = body.kept;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&cta_kept, k);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && cta_kept) atomicAdd(d.counter, (unsigned long long)cta_kept);
+}
+
 // ---- per-point-pair maps (IRLS weights, residual export) ------------------------------------------
 template <int STORE>
 struct WeightBody {
@@ -322,8 +386,10 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather(DevProblem d, int cou
 // which another block may be updating. The loss of a pair is counted by its first camera
 // only; each block writes the FP64 sum of its cameras' losses to cam_loss[block], and the
 // next kernel (pair setup or the finalize kernel) adds them up and advances the step count.
+template <bool FOCAL>
 __global__ void __launch_bounds__(STEP_CAMS * 32, 4)
 k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
+    constexpr int NV = FOCAL ? STEP_VALS : STEP_VALS - 1;   // sums carried per camera
     __shared__ float s_hi[STEP_VALS][STEP_CAMS], s_lo[STEP_VALS][STEP_CAMS];
     __shared__ int4 s_item[STEP_CAMS][32];
     __shared__ __align__(16) float s_geo[STEP_CAMS][32][GEO];
@@ -397,16 +463,16 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
                 const float4 sa = sl[0], sb = sl[1], sc = sl[2];
                 const float sum[10] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w, sc.x, sc.y};
                 float contrib[STEP_VALS];
-                pair_chain_rule(s_geo[warp][lo_i], it.z, sum, gscale, lscale, contrib);
+                pair_chain_rule<FOCAL>(s_geo[warp][lo_i], it.z, sum, gscale, lscale, contrib);
 #pragma unroll
-                for (int q = 0; q < STEP_VALS; ++q) two_sum_acc(hi[q], lo[q], contrib[q], 0.f);
+                for (int q = 0; q < NV; ++q) two_sum_acc(hi[q], lo[q], contrib[q], 0.f);
             }
         }
-        warp_two_sum_reduce<STEP_VALS>(hi, lo);
+        warp_two_sum_reduce<NV>(hi, lo);
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < STEP_VALS; ++q) {
-                s_hi[q][warp] = hi[q];
+                s_hi[q][warp] = q < NV ? hi[q] : 0.f;
                 s_lo[q][warp] = lo[q];
             }
         }
@@ -415,7 +481,7 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
     if (warp == 0 && lane < STEP_CAMS) {
         const int kc = blockIdx.x * STEP_CAMS + lane;
         const double bl = kc < d.n_cams
-            ? camera_update(d, kc, &s_hi[0][lane], &s_lo[0][lane], STEP_CAMS, s_mv[lane], s_Rc[lane], s_hyper,
+            ? camera_update<FOCAL>(d, kc, &s_hi[0][lane], &s_lo[0][lane], STEP_CAMS, s_mv[lane], s_Rc[lane], s_hyper,
                             t_step, apply, d.cam + (size_t)kc * CAMREC)
             : 0.0;
         s_loss[lane] = bl;
@@ -528,6 +594,12 @@ void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl) {
     }
 }
 
+void launch_stream_reweight(const DevProblem &d, cudaStream_t s, bool pdl) {
+    const dim3 grid(blocks_for(d.n_ranges, CTA_WARPS)), block(CTA_WARPS * 32);
+    if (d.storage == FM_STORE_FP32) launch_k(k_stream_reweight<FM_STORE_FP32>, grid, block, s, pdl, d);
+    else launch_k(k_stream_reweight<FM_STORE_FP16>, grid, block, s, pdl, d);
+}
+
 void launch_combine(const DevProblem &d, cudaStream_t s) {
     const double Z = d.z > 0.0 ? d.z : (double)d.n_pp;
     float gscale, lscale;
@@ -564,8 +636,12 @@ void launch_apply_gradient(const DevProblem &d, cudaStream_t s) {
 void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl) {
     float gscale, lscale;
     loss_scales(d, gscale, lscale);
-    launch_k(k_camera_step, dim3(blocks_for(d.n_cams, STEP_CAMS)), dim3(STEP_CAMS * 32), s, pdl, d,
-             gscale, lscale, apply ? 1 : 0);
+    if (d.refine_focal)
+        launch_k(k_camera_step<true>, dim3(blocks_for(d.n_cams, STEP_CAMS)), dim3(STEP_CAMS * 32), s, pdl, d,
+                 gscale, lscale, apply ? 1 : 0);
+    else
+        launch_k(k_camera_step<false>, dim3(blocks_for(d.n_cams, STEP_CAMS)), dim3(STEP_CAMS * 32), s, pdl, d,
+                 gscale, lscale, apply ? 1 : 0);
 }
 
 void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s) {

@@ -153,8 +153,10 @@ __global__ void k_quad_combine(DevProblem d) {
 // records to cam_dst: the records of this step's poses stay intact in cam_src for the other
 // blocks. The Adam step count is *d.step + 1 + it; the launch that closes the chain adds
 // the chain's length to *d.step.
+template <bool FOCAL>
 __global__ void __launch_bounds__(STEP_CAMS * 32, 4)
 k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gscale, float lscale, int apply) {
+    constexpr int NV = FOCAL ? STEP_VALS : STEP_VALS - 1;   // sums carried per camera
     __shared__ float s_hi[STEP_VALS][STEP_CAMS], s_lo[STEP_VALS][STEP_CAMS];
     __shared__ float s_mv[STEP_CAMS][12];
     __shared__ double s_Rc[STEP_CAMS][12];
@@ -244,15 +246,15 @@ k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gs
             for (int a = 0; a < 9; ++a) loss = fmaf(dv[a], q[a], loss);
             const float sum[10] = {q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8], loss};
             float contrib[STEP_VALS];
-            pair_chain_rule(g, role, sum, gscale, lscale, contrib);
+            pair_chain_rule<FOCAL>(g, role, sum, gscale, lscale, contrib);
 #pragma unroll
-            for (int w = 0; w < STEP_VALS; ++w) two_sum_acc(hi[w], lo[w], contrib[w], 0.f);
+            for (int w = 0; w < NV; ++w) two_sum_acc(hi[w], lo[w], contrib[w], 0.f);
         }
-        warp_two_sum_reduce<STEP_VALS>(hi, lo);
+        warp_two_sum_reduce<NV>(hi, lo);
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < STEP_VALS; ++q) {
-                s_hi[q][warp] = hi[q];
+                s_hi[q][warp] = q < NV ? hi[q] : 0.f;
                 s_lo[q][warp] = lo[q];
             }
         }
@@ -261,7 +263,7 @@ k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gs
     if (warp == 0 && lane < STEP_CAMS) {
         const int kc = blockIdx.x * STEP_CAMS + lane;
         const double bl = kc < d.n_cams
-            ? camera_update(d, kc, &s_hi[0][lane], &s_lo[0][lane], STEP_CAMS, s_mv[lane], s_Rc[lane], s_hyper,
+            ? camera_update<FOCAL>(d, kc, &s_hi[0][lane], &s_lo[0][lane], STEP_CAMS, s_mv[lane], s_Rc[lane], s_hyper,
                             t_step, apply, cam_dst + (size_t)kc * CAMREC)
             : 0.0;
         s_loss[lane] = bl;
@@ -295,8 +297,12 @@ void launch_quad_step(const DevProblem &d, int it, const float *cam_src, float *
                       cudaStream_t s, bool pdl) {
     float gscale, lscale;
     loss_scales(d, gscale, lscale);
-    launch_k(k_quad_step, dim3(camera_step_blocks(d)), dim3(STEP_CAMS * 32), s, pdl, d, it, cam_src, cam_dst,
-             gscale, lscale, apply ? 1 : 0);
+    if (d.refine_focal)
+        launch_k(k_quad_step<true>, dim3(camera_step_blocks(d)), dim3(STEP_CAMS * 32), s, pdl, d, it, cam_src,
+                 cam_dst, gscale, lscale, apply ? 1 : 0);
+    else
+        launch_k(k_quad_step<false>, dim3(camera_step_blocks(d)), dim3(STEP_CAMS * 32), s, pdl, d, it, cam_src,
+                 cam_dst, gscale, lscale, apply ? 1 : 0);
 }
 
 }  // namespace fm

@@ -102,6 +102,9 @@ __device__ __forceinline__ void orthonormalize_rows(double *R) {
 // camera only) the loss in contrib[6], and in contrib[7] the gradient with respect to the
 // camera's keypoint scale s: with F = S_j E S_i, dL/dE = S_j G S_i (G = dL/dF) and
 // dL/ds_i = sum_{a, b<2} G_ab E_ab (S_j)_a, dL/ds_j = sum_{a<2, b} G_ab E_ab (S_i)_b.
+// FOCAL = false: the scale gradient is not formed (contrib[7] = 0); the pair matrix still
+// carries the scales, so dL/dE = S_j G S_i either way.
+template <bool FOCAL>
 __device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const float *sum,
                                                 float gscale, float lscale, float *contrib) {
     float Gp[9];
@@ -129,22 +132,24 @@ __device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const
     // focal: E = [th]_x R_n, the scale gradient from G = dL/dF, then G <- dL/dE
     const float s_i = gr[35], s_j = gr[36];
     {
-        float E[9];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            E[b] = -th[2] * Rn[3 + b] + th[1] * Rn[6 + b];
-            E[3 + b] = th[2] * Rn[b] - th[0] * Rn[6 + b];
-            E[6 + b] = -th[1] * Rn[b] + th[0] * Rn[3 + b];
-        }
         const float si[3] = {s_i, s_i, 1.f}, sj[3] = {s_j, s_j, 1.f};
         float gs = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
+        if (FOCAL) {
+            float E[9];
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                const float ge = G[3 * a + b] * E[3 * a + b];
-                if (role == 0 ? b < 2 : a < 2) gs = fmaf(ge, role == 0 ? sj[a] : si[b], gs);
+                E[b] = -th[2] * Rn[3 + b] + th[1] * Rn[6 + b];
+                E[3 + b] = th[2] * Rn[b] - th[0] * Rn[6 + b];
+                E[6 + b] = -th[1] * Rn[b] + th[0] * Rn[3 + b];
             }
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const float ge = G[3 * a + b] * E[3 * a + b];
+                    if (role == 0 ? b < 2 : a < 2) gs = fmaf(ge, role == 0 ? sj[a] : si[b], gs);
+                }
+        }
         contrib[7] = gs;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -221,6 +226,7 @@ __device__ __forceinline__ void warp_two_sum_reduce(float *hi, float *lo) {
 // scale gradient) `stride` apart; mv = the camera's Adam m (6) and v (6); Rc = its R (9) and
 // c (3); hyper = lr_rot, lr_c, beta1, beta2, eps, lr_focal. With focal refinement rho = log s
 // takes its own Adam step (gradient s dL/ds). Returns the camera's loss share.
+template <bool FOCAL>
 __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, const float *hi, const float *lo,
                                                 int stride, const float *mv, const double *Rc,
                                                 const double *hyper, long long t_step, int apply,
@@ -235,7 +241,7 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
     if (!ok) atomicOr(d.err, ERR_NONFINITE);
     const double bl = (double)hi[6 * stride] + (double)lo[6 * stride];
     const double s_cur = camera_scale(d, kc);
-    const double g_rho = s_cur * ((double)hi[7 * stride] + (double)lo[7 * stride]);
+    const double g_rho = FOCAL ? s_cur * ((double)hi[7 * stride] + (double)lo[7 * stride]) : 0.0;
     if (!apply) {
 #pragma unroll
         for (int q = 0; q < 6; ++q) d.grad[(size_t)kc * 6 + q] = g[q];
@@ -246,7 +252,7 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
     const float b1 = (float)hyper[2], b2 = (float)hyper[3], eps = (float)hyper[4];
     const float lr_r = (float)hyper[0], lr_c = (float)hyper[1];
     const float bc1 = 1.f - powf(b1, (float)t_step), bc2 = 1.f - powf(b2, (float)t_step);
-    if (d.refine_focal) {
+    if (FOCAL) {
         const float gq = (float)g_rho;
         const float mo = b1 * d.rho_m[kc] + (1.f - b1) * gq;
         const float vo = b2 * d.rho_v[kc] + (1.f - b2) * gq * gq;

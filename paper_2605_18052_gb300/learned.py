@@ -161,8 +161,7 @@ def time_to_accuracy(sc, arm: str, net: Mlp | None = None, storage: str = "fp16"
             s = sch.decay ** r
             gp.set_learning_rate(sch.lr_rot * s, sch.lr_c * s)
             if arm == "irls":
-                gp.irls_weights(tau)
-                gp.step(sch.iters_per_round)
+                gp.step_irls(tau, sch.iters_per_round)
             elif arm == "irls_quad":
                 gp.irls_preaggregate(tau)
                 gp.step_quadratic(sch.iters_per_round)

@@ -3,7 +3,7 @@
 Each round reweights the point pairs at the current poses with a filtering threshold that
 starts large and shrinks by a constant factor every round down to a floor, then runs a fixed
 number of Adam iterations on the reweighted objective. All per-point-pair work happens inside the library
-calls (fm_irls_weights, fm_step).
+calls (fm_step_irls: the reweighting fused into the round's first pass over the point pairs).
 
 With `quadratic=True` a round makes one pass over the point pairs (reweighting and the
 per-image-pair quadratic form of the reweighted objective, fm_irls_preaggregate) and its
@@ -49,8 +49,7 @@ def refine(problem, schedule: Schedule, callback=None, first_round: int = 0, qua
             problem.irls_preaggregate(schedule.tau(r))
             problem.step_quadratic(schedule.iters_per_round)
         else:
-            problem.irls_weights(schedule.tau(r))
-            problem.step(schedule.iters_per_round)
+            problem.step_irls(schedule.tau(r), schedule.iters_per_round)
         if callback is not None:
             callback(r, problem)
     return problem

@@ -360,3 +360,25 @@ def test_two_shards_on_one_gpu_sum_to_the_whole_problem():
     assert ang.max() < 1e-3
     for s in shards:
         s.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("tau", [0.05, math.inf])
+def test_fused_reweighting_round_is_bit_identical(storage, tau):
+    # fm_step_irls = fm_irls_weights + fm_step with the reweighting inside the first pass
+    sc = _scene("sphere128", seed=3)
+    R0, t0 = sc.R_init.numpy(), sc.t_init.numpy()
+    res = []
+    for fused in (False, True):
+        with _gpu_problem(sc, R0, t0, storage=storage) as gp:
+            if fused:
+                kept = gp.step_irls(tau, 9, count=True)
+            else:
+                kept = gp.irls_weights(tau)
+                gp.step(9)
+            res.append((kept, gp.get_weights(), gp.get_params(), gp.last_loss(), gp.get_state()[2]))
+    (k0, w0, p0, l0, s0), (k1, w1, p1, l1, s1) = res
+    assert k0 == k1 and s0 == s1 == 9 and l0 == l1
+    np.testing.assert_array_equal(w0, w1)
+    np.testing.assert_array_equal(p0[0], p1[0])
+    np.testing.assert_array_equal(p0[1], p1[1])
