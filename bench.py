@@ -307,6 +307,71 @@ def cpu_oracle_rate(sc, seconds: float):
     return evals * npp / el / 1e9, f"first {nb} image pairs ({npp} point pairs), {evals} loss+grad evaluations"
 
 
+def _oracle_worker(args):
+    """One process of the all-cores CPU baseline: the oracle's loss+gradient on its share of
+    the sample, repeated for `seconds`; returns point pairs evaluated and the elapsed time."""
+    n_cams, ci, cj, pid, x1, x2, R0, c0, seconds = args
+    import numpy as np
+    import oracle as O
+    prob = O.Problem(n_cams, ci, cj, pid, x1, x2)
+    w = np.ones(pid.shape[0])
+    evals = 0
+    t0 = time.perf_counter()
+    while True:
+        O.loss_grad(prob, R0, c0, w)
+        evals += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return evals * pid.shape[0], el
+
+
+def cpu_oracle_rate_all_cores(sc, seconds: float):
+    """The same oracle, one process per host core, each on a disjoint block of whole image
+    pairs of the same sample (processes started with spawn: this runs after CUDA work)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import numpy as np
+    cores = os.cpu_count() or 1
+    cnt = np.bincount(sc.pair_id.cpu().numpy(), minlength=sc.n_pairs)
+    target = 4_000_000
+    nb = min(int(np.searchsorted(np.cumsum(cnt), target)) + 1, sc.n_pairs)
+    off = np.concatenate([[0], np.cumsum(cnt[:nb])])
+    cuts = np.linspace(0, nb, cores + 1).astype(int)
+    pid_all = sc.pair_id.cpu().numpy()
+    x1_all, x2_all = sc.x1.cpu().numpy(), sc.x2.cpu().numpy()
+    ci_all, cj_all = sc.cam_i.cpu().numpy(), sc.cam_j.cpu().numpy()
+    R0 = sc.R_init.cpu().numpy()
+    c0 = -(np.einsum("nba,nb->na", R0, sc.t_init.cpu().numpy()))
+    jobs = []
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        if b <= a:
+            continue
+        lo, hi = int(off[a]), int(off[b])
+        jobs.append((sc.n_cams, ci_all[a:b], cj_all[a:b], pid_all[lo:hi] - a, x1_all[lo:hi], x2_all[lo:hi],
+                     R0, c0, seconds))
+    with cf.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_worker, jobs))
+    pp = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    return pp / el / 1e9, len(jobs)
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "processor\t")) and ":" in line:
+                    v = line.split(":", 1)[1].strip()
+                    if v and not v.isdigit():
+                        import platform
+                        return f"{platform.machine()} {v}"
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def run_reference(args, rank):
     import torch
     import scenegen
@@ -501,7 +566,14 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, sample = cpu_oracle_rate(sc, args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "host_cores": os.cpu_count(), "cpu_model": cpu_model()}
+        try:
+            va, procs = cpu_oracle_rate_all_cores(sc, args.cpu_seconds)
+            cpu["all_cores"] = {"value": va, "unit": UNIT, "cores": procs,
+                                "sample": "the same image pairs split into one block per process"}
+        except Exception as e:   # a host that cannot start processes keeps the 1-thread figure
+            cpu["all_cores"] = {"unavailable": str(e)[:200]}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
