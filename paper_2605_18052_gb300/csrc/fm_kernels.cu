@@ -99,7 +99,7 @@ struct ReweightLossBody {
     __device__ __forceinline__ void point(int k, float e, float x1, float y1, float x2, float y2, float) {
         const float a = fabsf(e);
         const bool keep = a <= tau;  // NaN residuals are filtered
-        const float wf = keep ? 1.0f / fmaxf(a, delta) : 0.f;
+        const float wf = keep ? irls_weight(a, delta) : 0.f;
         const float w = STORE == FM_STORE_FP32 ? wf : __half2float(__float2half_rn(wf * scale));
         out[k] = w;
         kept += keep ? 1u : 0u;
@@ -159,7 +159,7 @@ struct WeightBody {
         const float a = fabsf(e);
         // filtered (w = 0) when |eps| > tau; NaN residuals are filtered too
         const bool keep = a <= tau;
-        out[k] = keep ? 1.0f / fmaxf(a, delta) : 0.f;
+        out[k] = keep ? irls_weight(a, delta) : 0.f;
         kept += keep ? 1u : 0u;
     }
     __device__ __forceinline__ void segment_begin(int) {}

@@ -39,7 +39,7 @@ struct QuadBody {
         if (REWEIGHT) {
             const float ae = fabsf(e);
             const bool keep = ae <= tau;  // NaN residuals are filtered
-            const float wf = keep ? 1.0f / fmaxf(ae, delta) : 0.f;
+            const float wf = keep ? irls_weight(ae, delta) : 0.f;
             w = STORE == FM_STORE_FP32 ? wf : __half2float(__float2half_rn(wf * scale));
             out[k] = w;
             kept += keep ? 1u : 0u;

@@ -132,6 +132,13 @@ __device__ __forceinline__ float epi(const float *E, float x1, float y1, float x
     return fmaf(x2, r0, fmaf(y2, r1, r2));
 }
 
+// IRLS weight 1/max(|eps|, delta) of a kept point pair. The fast reciprocal (within 2 ulp of
+// the rounded quotient; its argument is at least delta, far from the ranges where it differs
+// more) is used by every kernel that computes weights, so they agree with each other bit for
+// bit; against the exact quotient the difference is far inside the weight tolerance, which is
+// set by the residual's FP32 error.
+__device__ __forceinline__ float irls_weight(float a, float delta) { return __fdividef(1.0f, fmaxf(a, delta)); }
+
 // ---- the streaming walk ------------------------------------------------------------------------
 // Warp `r` streams point pairs [r*WR, min((r+1)*WR, n_pp)). Lane l of group g handles PPL
 // consecutive point pairs at g*32*PPL + l*PPL, so every load instruction of the warp reads one
