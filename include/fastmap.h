@@ -181,8 +181,9 @@ FM_API fm_status fm_residuals(fm_problem *p, float *eps);
 /*
  * n_iters optimiser iterations, each: objective gradient at the current poses, one Adam
  * step on (phi_k, c_k) (FP32 moments), R_k <- Exp(phi_k) R_k with FP64 exponential map and
- * re-orthonormalisation, c_k updated in FP64. Only
- * enqueues work; errors found on the device surface at the next synchronising call.
+ * re-orthonormalisation, c_k updated in FP64 (with opt.refine_focal also rho_k, see the focal
+ * section below). Only enqueues work; errors found on the device surface at the next
+ * synchronising call.
  */
 FM_API fm_status fm_step(fm_problem *p, int32_t n_iters);
 
@@ -209,14 +210,16 @@ FM_API fm_status fm_apply_gradient(fm_problem *p, const double *grad, int32_t on
 /* Change the Adam step sizes used by later iterations (a learning-rate schedule). */
 FM_API fm_status fm_set_learning_rate(fm_problem *p, double lr_rot, double lr_c);
 
-/* Zero the Adam moments and the step counter. */
+/* Zero the Adam moments (poses and focal scales) and the step counter. */
 FM_API fm_status fm_reset_optimizer(fm_problem *p);
 
 /*
  * Optimiser state for checkpoint/resume: m and v (n_cams x 6, host FP64 arrays; the device
  * keeps them in FP32, so values round-trip exactly when they came from fm_get_state) and the
- * number of Adam steps taken. Resuming from a saved (poses, weights, state) gives
- * bit-identical trajectories because every reduction runs in a fixed order.
+ * number of Adam steps taken. Resuming from a saved (poses, weights, state) gives bit-identical
+ * trajectories because every reduction runs in a fixed order. (With focal refinement the scales
+ * are saved and restored with fm_get_focal_scales / fm_set_focal_scales, which resets their
+ * moments, so such a resume is not bit-identical.)
  */
 FM_API fm_status fm_get_state(fm_problem *p, double *m, double *v, int64_t *step);
 FM_API fm_status fm_set_state(fm_problem *p, const double *m, const double *v, int64_t step);
