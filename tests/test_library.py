@@ -120,3 +120,43 @@ def test_rotation_rejects_bad_host_arguments_without_a_gpu(lib):
         with pytest.raises(fm.FastMapError) as ei:
             fm.Rotation(c["cam_i"], c["cam_j"], c["R_rel"], c["n"])
         assert ei.value.status == -1
+
+
+def test_header_compiles_as_c_and_links_without_a_gpu(lib, tmp_path):
+    # a plain C caller of the boundary: includes the header, links libfastmap.so, and exercises
+    # the calls that need no device (defaults, status strings, argument validation)
+    src = tmp_path / "caller.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "fastmap.h"
+int main(void) {
+    fm_options o;
+    fm_default_options(&o);
+    if (o.storage != FM_STORE_FP32 || o.loss != FM_LOSS_IRLS || o.refine_focal != 0) return 1;
+    double R[18] = {1,0,0, 0,1,0, 0,0,1,  1,0,0, 0,1,0, 0,0,1};
+    double t[6] = {0,0,0, 1,0,0};
+    int ci[1] = {0}, cj[1] = {0};                 /* cam_i == cam_j: rejected before any CUDA call */
+    int pid[2] = {0, 0};
+    float x[4] = {0, 0, 0, 0};
+    fm_problem *p = NULL;
+    fm_status st = fm_create_problem(2, R, t, 1, ci, cj, 2, pid, x, x, 0, &o, NULL, &p);
+    if (st != FM_EINVAL || p != NULL) return 2;
+    if (strlen(fm_last_error()) == 0 || strlen(fm_status_string(FM_EINVAL)) == 0) return 3;
+    fm_translation_options to;
+    fm_translation_default_options(&to);
+    fm_rotation_options ro;
+    fm_rotation_default_options(&ro);
+    if (!(to.lr > 0) || !(ro.cg_tol > 0) || fm_mlp_num_params() != 1377) return 4;
+    printf("ok\n");
+    return 0;
+}
+''')
+    so_dir = os.path.dirname(binding.library_path()) if hasattr(binding, "library_path") else \
+        os.path.join(ROOT, "paper_2605_18052_gb300")
+    exe = tmp_path / "caller"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-L", so_dir, "-lfastmap", "-o", str(exe)], check=True)
+    env = dict(os.environ, LD_LIBRARY_PATH=so_dir + ":" + os.environ.get("LD_LIBRARY_PATH", ""))
+    out = subprocess.run([str(exe)], capture_output=True, text=True, env=env)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
