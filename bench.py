@@ -372,6 +372,15 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
+def bench_config(args, sc, world: int) -> dict:
+    """The workload description both arms report."""
+    return {"workload": f"{args.config}: {sc.n_cams} cameras, {sc.n_pairs} image pairs, {sc.n_pp} point pairs",
+            "storage": args.storage, "iters_per_step": args.iters,
+            "step": "1 IRLS round: reweighting (fused into the first pass) + iters x (loss+grad, Adam)",
+            "l2": "inputs larger than L2 (no flush needed)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank):
     import torch
     import scenegen
@@ -393,8 +402,8 @@ def run_reference(args, rank):
            "ms_per_step": args.iters * npp_total / (value * 1e9) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded scene generator)",
-           "config": {"workload": f"{args.config} (FP64 CPU oracle, 1 thread)", "n_pp": npp_total,
-                      "n_pairs": sc.n_pairs, "n_cams": sc.n_cams, "iters_per_step": args.iters},
+           "config": bench_config(args, sc, args.gpus),
+           "implementation": "FP64 CPU oracle (plain C loops), 1 thread, on a bounded sample of the workload",
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -580,11 +589,7 @@ def main():
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded scene generator, trajectory scene shaped like the paper's large scenes)",
-               "config": {"workload": f"{args.config}: {sc.n_cams} cameras, {sc.n_pairs} image pairs, {n_pp} point pairs",
-                          "storage": args.storage, "iters_per_step": args.iters,
-                          "step": "1 IRLS round: reweighting (fused into the first pass) + iters x (loss+grad, Adam)",
-                          "l2": "inputs larger than L2 (no flush needed)",
-                          "parallelism": f"replicas x{world}"},
+               "config": bench_config(args, sc, world),
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "time_to_accuracy": tta, "quadratic_path": quad, "global_translation": trans,
                "global_rotation": rot,
