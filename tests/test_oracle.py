@@ -5,7 +5,6 @@ import math
 
 import numpy as np
 import pytest
-import torch
 
 import oracle as O
 import scenegen
