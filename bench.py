@@ -1,8 +1,9 @@
 """Benchmark of the epipolar-adjustment hot path on GB300.
 
 One step = one IRLS round of the method: reweighting with filtering at the current poses
-(fm_irls_weights) followed by `--iters` optimiser iterations (loss + analytic gradient over
-every point pair, per-camera gradient, Adam + exponential map), all on the GPU.
+followed by `--iters` optimiser iterations (loss + analytic gradient over every point pair,
+per-camera gradient, Adam + exponential map), all on the GPU (fm_step_irls: the reweighting
+is fused into the round's first pass).
 
 Default workload: the 4,000-camera trajectory scene (~1.5e8 point pairs, ~5e4 image pairs,
 Pareto match counts, 25% outliers), FP16 centroid-offset storage, FP32 arithmetic. The
@@ -46,6 +47,7 @@ def parse():
     ap.add_argument("--no-tta", action="store_true", help="skip the time-to-accuracy comparison")
     ap.add_argument("--no-quad", action="store_true", help="skip the quadratic-form timing")
     ap.add_argument("--no-translation", action="store_true", help="skip the global-translation timing")
+    ap.add_argument("--no-focal", action="store_true", help="skip the focal-refinement timing")
     ap.add_argument("--tta-config", default="traj1000_o30")
     ap.add_argument("--tta-rounds", type=int, default=120)
     return ap.parse_args()
@@ -281,6 +283,35 @@ def rotation_section(sc, stream, iters: int = 500):
     return out
 
 
+def focal_section(args, sc, sch, stream, n_pp: int, pose_only_ms: float):
+    """The benchmark's step with refine_focal=1 on a second problem over the same point pairs."""
+    import torch
+    import paper_2605_18052_gb300 as fm
+    gf = fm.Problem(sc.R_init.cpu(), sc.t_init.cpu(), sc.cam_i.cpu(), sc.cam_j.cpu(), sc.pair_id,
+                    sc.x1, sc.x2, options=sch.options(storage=args.storage, refine_focal=1))
+    try:
+        for r in range(args.warmup):
+            gf.step_irls(sch.tau(r % sch.rounds), args.iters)
+        gf.synchronize()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in range(args.steps):
+            gf.step_irls(sch.tau((args.warmup + k) % sch.rounds), args.iters)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        f_ms = f0.elapsed_time(f1) / args.steps
+        s = gf.focal_scales()
+    finally:
+        gf.close()
+    return {"value": float(n_pp) * args.iters / (f_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": f_ms,
+            "time_vs_pose_only": f_ms / pose_only_ms,
+            "scales_min_max": [float(s.min()), float(s.max())],
+            "note": "same step (1 fused IRLS round + iters iterations) with the focal scales s_k optimised "
+                    "with the poses; the point pairs are those of the pose-only line"}
+
+
 def cpu_oracle_rate(sc, seconds: float):
     """FP64 oracle loss+gradient on a bounded sample of whole image pairs (1 thread)."""
     import numpy as np
@@ -388,11 +419,12 @@ def run_reference(args, rank):
         return
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     sc = scenegen.make_scene(args.config, seed=args.seed, device=dev).to("cpu")
-    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    # about 6 x --cpu-seconds of oracle work over the whole run (a minute by default)
+    per_step = 6.0 * args.cpu_seconds / max(1, args.steps + args.warmup)
     vals = []
     sample = ""
     for k in range(args.warmup + args.steps):
-        v, sample = cpu_oracle_rate(sc, per_step if k >= args.warmup else 0.5)
+        v, sample = cpu_oracle_rate(sc, per_step if k >= args.warmup else min(0.5, per_step))
         if k >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
@@ -538,6 +570,15 @@ def main():
                         "per-image-pair quadratic form; equivalent_value counts the point pairs the "
                         "streaming path would have read"}
 
+    # the same rounds with the focal lengths refined together with the poses (F = S_j E S_i):
+    # the streaming pass reads the same bytes, the camera step also moves rho_k = log s_k
+    focal = None
+    if not args.no_focal:
+        try:
+            focal = focal_section(args, sc, sch, stream, n_pp, ms_max / args.steps)
+        except Exception as e:   # recorded; the main line stands
+            focal = {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
+
     # end to end through the public API with pinned host buffers: create + full schedule + poses
     e2e = None
     if not args.no_e2e:
@@ -592,7 +633,7 @@ def main():
                "config": bench_config(args, sc, world),
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "time_to_accuracy": tta, "quadratic_path": quad, "global_translation": trans,
-               "global_rotation": rot,
+               "global_rotation": rot, "focal_refinement": focal,
                "clocks": clocks, "hbm_frac_of_step": value * 1e9 * bytes_per_launch / n_pp / 1e9 / peak}
         print(json.dumps(out))
     if world > 1:
