@@ -7,9 +7,10 @@ reweighting step of the IRLS loop (Sec. "Epipolar Adjustment") then uses
 w = p / max(|eps^|, delta) in place of the hard threshold mask. Labels come from the method
 itself: the IRLS mask |eps| <= tau_min at the poses a long plain-IRLS run converged to.
 
-Everything here is plain FP64 NumPy, written for checking the CUDA kernels; parity of the
-training result itself is unpinned (it depends on data and initialisation), the forward and
-backward passes are pinned by finite differences in the tests.
+Everything here is plain FP64 NumPy, written for checking the CUDA kernels. The trained
+network itself: parity unpinned (it depends on data and initialisation; its only judge is the
+pose error it reaches). The forward and backward passes are pinned by finite differences in
+the tests.
 """
 from __future__ import annotations
 
