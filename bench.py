@@ -34,7 +34,7 @@ UNIT = "G point-pairs/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="traj4000")
@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-quad", action="store_true", help="skip the quadratic-form timing")
     ap.add_argument("--no-translation", action="store_true", help="skip the global-translation timing")
     ap.add_argument("--no-focal", action="store_true", help="skip the focal-refinement timing")
+    ap.add_argument("--clocks-csv", default=None, help="keep nvidia-smi's clock samples in this file")
     ap.add_argument("--tta-config", default="traj1000_o30")
     ap.add_argument("--tta-rounds", type=int, default=120)
     return ap.parse_args()
@@ -94,15 +95,29 @@ def profiled_traffic(kernel_tag: str):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples while the timed region runs."""
+    """nvidia-smi clock/throttle samples while the timed region runs.
 
-    def __init__(self, index: int):
+    The sampler is started before the timed region and waits (at most 3 s) for nvidia-smi's
+    first line; only lines written after that count, so every sample is taken while timed
+    work runs. The raw samples go to `path` (a temporary file unless --clocks-csv names one).
+    """
+
+    def __init__(self, index: int, path: str | None = None):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.skip = 0
+        self.path = path or os.path.join(tempfile.gettempdir(), f"fm_bench_clocks_rank{index}_{os.getpid()}.csv")
+
+    def _lines(self) -> int:
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -113,6 +128,11 @@ class ClockSampler:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        t0 = time.perf_counter()
+        while self._lines() == 0 and self.proc.poll() is None and time.perf_counter() - t0 < 3.0:
+            time.sleep(0.02)
+        self.skip = self._lines()   # written before the timed region started
         return self
 
     def __exit__(self, *exc):
@@ -127,22 +147,34 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        with open(self.path) as fh:
+            lines = fh.readlines()
+
+        def parse(rows):
+            sm, mx, reasons = [], None, set()
+            for line in rows:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            return sm, mx, reasons
+
+        sm, mx, reasons = parse(lines[self.skip:])
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if not sm:   # region shorter than the 200 ms period: the sample just before it
+            sm, mx, reasons = parse(lines[:self.skip][-1:])
+            out.update({"sm_mhz": sm[0] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                        "note": "timed region shorter than the sampling period; sample taken just before it"})
+        return out
 
 
 def schedule_for(sc, iters):
@@ -312,8 +344,9 @@ def focal_section(args, sc, sch, stream, n_pp: int, pose_only_ms: float):
                     "with the poses; the point pairs are those of the pose-only line"}
 
 
-def cpu_oracle_rate(sc, seconds: float):
-    """FP64 oracle loss+gradient on a bounded sample of whole image pairs (1 thread)."""
+def oracle_sample(sc):
+    """The CPU baseline's sample: the first whole image pairs up to 4 M point pairs, as an
+    oracle problem, with the initial poses."""
     import numpy as np
     import oracle as O
     cnt = np.bincount(sc.pair_id.cpu().numpy(), minlength=sc.n_pairs)
@@ -326,6 +359,14 @@ def cpu_oracle_rate(sc, seconds: float):
                      sc.x1[:npp].cpu().numpy(), sc.x2[:npp].cpu().numpy())
     R0 = sc.R_init.cpu().numpy()
     c0 = O.centres_from_poses(R0, sc.t_init.cpu().numpy())
+    return prob, R0, c0, nb, npp
+
+
+def cpu_oracle_rate(sc, seconds: float, sample=None):
+    """FP64 oracle loss+gradient on a bounded sample of whole image pairs (1 thread)."""
+    import numpy as np
+    import oracle as O
+    prob, R0, c0, nb, npp = sample if sample is not None else oracle_sample(sc)
     w = np.ones(npp)
     evals = 0
     t0 = time.perf_counter()
@@ -423,8 +464,9 @@ def run_reference(args, rank):
     per_step = 6.0 * args.cpu_seconds / max(1, args.steps + args.warmup)
     vals = []
     sample = ""
+    prepared = oracle_sample(sc)
     for k in range(args.warmup + args.steps):
-        v, sample = cpu_oracle_rate(sc, per_step if k >= args.warmup else min(0.5, per_step))
+        v, sample = cpu_oracle_rate(sc, per_step if k >= args.warmup else min(0.5, per_step), prepared)
         if k >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
@@ -488,7 +530,7 @@ def main():
         dist.barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_csv) as clk:
         # timed region: the production path (CUDA graphs of chained iterations)
         torch.cuda.synchronize()
         ev0.record(stream)
