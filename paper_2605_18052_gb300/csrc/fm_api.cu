@@ -165,14 +165,14 @@ void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed, bool first, bo
         launch_camera_step(p->d, true, s, true);
         return;
     }
-    if (timed) {
-        if (p->tev_used + 2 > p->tev.size()) {
-            for (int k = 0; k < 64; ++k) {
-                cudaEvent_t e;
-                cudaEventCreate(&e);
-                p->tev.push_back(e);
-            }
+    if (timed && p->tev_used + 2 > p->tev.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) break;   // reported by the call's error check
+            p->tev.push_back(e);
         }
+    }
+    if (timed && p->tev_used + 2 <= p->tev.size()) {
         cudaEventRecord(p->tev[p->tev_used], s);
         launch_stream_loss(p->d, s, false);
         cudaEventRecord(p->tev[p->tev_used + 1], s);
