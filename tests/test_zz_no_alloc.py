@@ -7,7 +7,8 @@ fm_loss_grad) with the parity tolerance used for the oracle (loss relative 1e-4,
 within 1e-4 of its largest entry), on two calls in a row of different sizes (stale scratch
 from the first call must not leak into the second), plus: a repeated call is bit-identical,
 device free memory does not change across a call, and sizes beyond the limits are refused.
-This file is collected last so a run that stops at the first failure has run everything else.
+This file is collected after the other parity files (only the full-size checks follow), so a
+run that stops at the first failure has run them first.
 """
 import ctypes
 
