@@ -160,3 +160,28 @@ int main(void) {
     env = dict(os.environ, LD_LIBRARY_PATH=so_dir + ":" + os.environ.get("LD_LIBRARY_PATH", ""))
     out = subprocess.run([str(exe)], capture_output=True, text=True, env=env)
     assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
+
+
+def test_missing_library_fails_loudly():
+    # a fresh interpreter whose loader points at a path that does not exist: every entry of
+    # the product path raises instead of computing anything another way
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import numpy as np\n"
+        "import paper_2605_18052_gb300 as fm\n"
+        "from paper_2605_18052_gb300 import binding\n"
+        "binding.load_library.__defaults__ = ('/nonexistent/libfastmap.so',)\n"
+        "R = np.tile(np.eye(3), (2, 1, 1)); t = np.array([[0., 0, 0], [1, 0, 0]])\n"
+        "calls = [lambda: fm.Problem(R, t, [0], [1], [0], np.zeros((1, 2), np.float32), np.zeros((1, 2), np.float32)),\n"
+        "         lambda: fm.default_options(), lambda: fm.Mlp(np.zeros(1377, np.float32)),\n"
+        "         lambda: fm.Rotation([0], [1], np.eye(3)[None], 2)]\n"
+        "for f in calls:\n"
+        "    try:\n"
+        "        f()\n"
+        "    except binding.FastMapError as e:\n"
+        "        assert 'missing' in str(e), e\n"
+        "    else:\n"
+        "        raise SystemExit('no error')\n"
+        "print('raised')\n" % ROOT)
+    r = subprocess.run(["python", "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "raised", r.stdout + r.stderr
