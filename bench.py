@@ -478,7 +478,8 @@ def run_reference(args, rank):
            "data": "synthetic (seeded scene generator)",
            "config": bench_config(args, sc, args.gpus),
            "implementation": "FP64 CPU oracle (plain C loops), 1 thread, on a bounded sample of the workload",
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "seconds_per_iteration": npp_total / (value * 1e9)},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -659,10 +660,12 @@ def main():
     if rank == 0 and not args.no_cpu:
         v, sample = cpu_oracle_rate(sc, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds_per_iteration": n_pp / (v * 1e9),
                "host_cores": os.cpu_count(), "cpu_model": cpu_model()}
         try:
             va, procs = cpu_oracle_rate_all_cores(sc, args.cpu_seconds)
             cpu["all_cores"] = {"value": va, "unit": UNIT, "cores": procs,
+                                "seconds_per_iteration": n_pp / (va * 1e9),
                                 "sample": "the same image pairs split into one block per process"}
         except Exception as e:   # a host that cannot start processes keeps the 1-thread figure
             cpu["all_cores"] = {"unavailable": str(e)[:200]}
