@@ -120,20 +120,23 @@ class Problem:
 
 # ---- pose conventions -----------------------------------------------------------------
 def centres_from_poses(R, t):
-    """c_k = -R_k^T t_k."""
+    """c_k = -R_k^T t_k: the camera centre of a world-to-camera pose (the translations of
+    Eq. epipolar-objective are optimised through it; a reading, see the module notes)."""
     R = _f64(R).reshape(-1, 3, 3)
     return -np.einsum("nba,nb->na", R, _f64(t).reshape(-1, 3))
 
 
 def poses_from_centres(R, c):
-    """t_k = -R_k c_k."""
+    """t_k = -R_k c_k, the inverse of centres_from_poses."""
     R = _f64(R).reshape(-1, 3, 3)
     return -np.einsum("nab,nb->na", R, _f64(c).reshape(-1, 3))
 
 
 # ---- objective --------------------------------------------------------------------------
 def essential(prob: Problem, R, c) -> np.ndarray:
-    """E_n = [t_n/|t_n|]_x R_j R_i^T for every pair, (B, 3, 3)."""
+    """E_n = [t_n/|t_n|]_x R_j R_i^T for every pair, (B, 3, 3): the essential matrix of image
+    pair n computed from the global poses (Eq. epipolar-objective; the unit translation is a
+    reading, see the module notes)."""
     R = _f64(R).reshape(-1, 9)
     c = _f64(c).reshape(-1, 3)
     E = np.empty((prob.n_pairs, 9))
@@ -143,7 +146,8 @@ def essential(prob: Problem, R, c) -> np.ndarray:
 
 
 def residuals(prob: Problem, R, c) -> np.ndarray:
-    """epsilon_nm = x2^T E_n x1 for every point pair, input order."""
+    """epsilon_nm = x2^T E_n x1 for every point pair, input order (the epipolar error inside
+    Eq. epipolar-objective)."""
     R = _f64(R).reshape(-1, 9)
     c = _f64(c).reshape(-1, 3)
     eps = np.empty(prob.n_pp)
@@ -181,7 +185,9 @@ def loss_grad(prob: Problem, R, c, w=None, mode: str = "irls"):
 
 
 def irls_weights(eps_hat, tau: float, delta: float):
-    """w = [|eps^| <= tau] / max(|eps^|, delta); returns (w, number kept)."""
+    """w = [|eps^| <= tau] / max(|eps^|, delta); returns (w, number kept). The IRLS weight
+    1/|eps^| of Sec. "Epipolar Adjustment" (IRLS paragraph; the floor delta is a reading) with
+    the filtering paragraph's threshold: pairs above tau get weight 0."""
     e = _f64(eps_hat)
     w = np.empty_like(e)
     kept = _load().or_irls_weights(e.shape[0], _p(e), float(tau), float(delta), _p(w))
@@ -196,6 +202,8 @@ def threshold_schedule(r: int, tau0: float, tau_min: float, factor: float = 0.8)
 
 # ---- optimiser ----------------------------------------------------------------------------
 def expmap(phi) -> np.ndarray:
+    """Exp(phi) of one rotation vector by Rodrigues' formula (the rotation increment of the
+    first-order loop, Sec. "First-order Optimization"); a series near 0 (epipolar.c)."""
     phi = _f64(phi).reshape(3)
     R = np.empty(9)
     _load().or_expmap(_p(phi), _p(R))
@@ -203,7 +211,8 @@ def expmap(phi) -> np.ndarray:
 
 
 def project_rotation(R) -> np.ndarray:
-    """Nearest rotation matrix (SVD polar factor with det +1), applied per camera."""
+    """Nearest rotation matrix (SVD polar factor with det +1), applied per camera: keeps the
+    rotations of the first-order loop (Sec. "First-order Optimization") on SO(3)."""
     R = _f64(R).reshape(-1, 3, 3)
     U, _, Vt = np.linalg.svd(R)
     d = np.sign(np.linalg.det(U @ Vt))
@@ -214,7 +223,9 @@ def project_rotation(R) -> np.ndarray:
 
 def adam_step(R, c, grad, m, v, step: int, lr_rot: float, lr_c: float,
               beta1=0.9, beta2=0.999, eps=1e-12):
-    """One Adam step in place on (R, c, m, v); R is re-orthonormalised afterwards."""
+    """One Adam step in place on (R, c, m, v); R is re-orthonormalised afterwards. Adam is the
+    adaptive first-order method Sec. "First-order Optimization" cites; rotations move by
+    R <- Exp(step) R, centres additively."""
     lr = np.array([lr_rot, lr_c], dtype=np.float64)
     _load().or_adam_step(R.shape[0], _p(R), _p(c), _p(_f64(grad)), _p(m), _p(v), int(step), _p(lr),
                          float(beta1), float(beta2), float(eps))
@@ -310,12 +321,14 @@ def fp16_centroid_storage(prob: Problem, x1_f32, x2_f32):
 
 
 def fp16_weight_scale(delta: float) -> float:
-    """Power-of-two scale s with (1/delta) * s <= 32768, so FP16 holds w * s without overflow."""
+    """Power-of-two scale s with (1/delta) * s <= 32768, so FP16 holds w * s without overflow
+    (the FP16 storage the CUDA path promises; not from the paper, which stores FP32)."""
     return 2.0 ** np.floor(np.log2(32768.0 * delta))
 
 
 def quantize_weights_fp16(w, delta: float) -> np.ndarray:
-    """w as stored by the FP16 path: fp16_rn(fp32(w) * s) / s."""
+    """w as stored by the FP16 path: fp16_rn(fp32(w) * s) / s (a storage rule of the CUDA
+    path, restated here so the oracle computes on the same weights)."""
     s = np.float32(fp16_weight_scale(delta))
     q = (np.asarray(w, dtype=np.float32) * s).astype(np.float16)
     return q.astype(np.float64) / float(s)
@@ -338,7 +351,8 @@ def rotation_error_deg(R_est, R_gt):
 
 
 def translation_error_deg(R_est, c_est, R_gt, c_gt, cam_i, cam_j):
-    """Angle between estimated and true unit relative translations t_n/|t_n| per pair."""
+    """Angle between estimated and true unit relative translations t_n/|t_n| per pair (the
+    relative-translation error the thesis' accuracy metrics cite)."""
     def tdir(R, c):
         R = _f64(R).reshape(-1, 3, 3)
         c = _f64(c).reshape(-1, 3)
