@@ -64,10 +64,12 @@ SHAPES = (("W1", (N_FEAT, HIDDEN)), ("b1", (HIDDEN,)), ("W2", (HIDDEN, HIDDEN)),
 
 
 def flatten(params) -> np.ndarray:
+    """Parameters as one vector in the library's order (W1, b1, W2, b2, W3, b3; row-major)."""
     return np.concatenate([np.asarray(params[k], np.float64).reshape(-1) for k, _ in SHAPES])
 
 
 def unflatten(vec) -> dict:
+    """The inverse of flatten."""
     vec = np.asarray(vec, np.float64)
     out, o = {}, 0
     for k, shp in SHAPES:
@@ -126,6 +128,8 @@ def bce_loss_grad_bf16(params, X, y):
 
 
 def init_params(seed=0):
+    """He-normal weights (variance 2/fan-in for the ReLU layers, 1/fan-in for the output) and
+    zero biases, seeded."""
     rng = np.random.default_rng(seed)
     return {
         "W1": rng.normal(0, np.sqrt(2.0 / N_FEAT), (N_FEAT, HIDDEN)),
@@ -170,10 +174,13 @@ def bce_loss_grad(params, X, y):
 
 
 def adam_init(params):
+    """Zero first and second moments for adam_update."""
     return {k: np.zeros_like(v) for k, v in params.items()}, {k: np.zeros_like(v) for k, v in params.items()}
 
 
 def adam_update(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma and Ba, bias-corrected; `step` is 1-based) on every parameter,
+    in place: the training optimiser of the network."""
     bc1 = 1 - beta1 ** step
     bc2 = 1 - beta2 ** step
     for k in params:

@@ -97,6 +97,8 @@ def rot_from_6d(a):
 
 
 def six_d_from_rot(R):
+    """The 6D parameters of rotations (their first two columns), the inverse of rot_from_6d
+    on SO(3) (6D representation of Sec. "Global Rotation")."""
     R = np.asarray(R, np.float64).reshape(-1, 3, 3)
     return np.concatenate([R[:, :, 0], R[:, :, 1]], axis=1)
 
@@ -128,6 +130,8 @@ def rot_6d_backward(a, gR):
 
 # ---- objective -------------------------------------------------------------------------------
 def geodesic(Ra, Rb):
+    """d(Ra, Rb) = arccos((tr(Ra^T Rb) - 1) / 2) per pair, radians (the geodesic distance of
+    Eq. fastmap-rotation-objective)."""
     c = (np.einsum("nab,nab->n", Ra, Rb) - 1.0) / 2.0
     return np.arccos(np.clip(c, -1.0, 1.0))
 
@@ -150,12 +154,16 @@ def loss_grad_R(R, cam_i, cam_j, R_rel):
 
 
 def loss_grad_6d(a, cam_i, cam_j, R_rel):
+    """L_R (Eq. fastmap-rotation-objective) and its gradient with respect to the 6D
+    parameters a (N, 6), by the chain rule through rot_from_6d."""
     R = rot_from_6d(a)
     loss, gR = loss_grad_R(R, cam_i, cam_j, R_rel)
     return loss, rot_6d_backward(a, gR)
 
 
 def adam(a0, cam_i, cam_j, R_rel, iters: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-12):
+    """`iters` Adam steps on the 6D parameters from a0 (the first-order optimisation of the
+    rotation objective, Sec. "Global Rotation"); returns (parameters, last loss)."""
     a = np.asarray(a0, np.float64).reshape(-1, 6).copy()
     m = np.zeros_like(a)
     v = np.zeros_like(a)
