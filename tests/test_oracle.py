@@ -266,6 +266,26 @@ def test_adam_first_step_closed_form():
     np.testing.assert_allclose(v, 0.001 * g * g)
 
 
+def test_adam_bias_correction_under_a_constant_gradient():
+    # with the same gradient every step, the bias-corrected moments are exactly g and g^2 at
+    # every step number, so each step moves every parameter by lr * sign(g); a wrong bias
+    # correction (or step count) changes the step length from the second step on
+    rng = np.random.default_rng(21)
+    g = rng.normal(size=(3, 6))
+    R = np.stack([O.expmap(rng.normal(size=3)) for _ in range(3)])
+    c = rng.normal(size=(3, 3))
+    m = np.zeros((3, 6))
+    v = np.zeros((3, 6))
+    R0, c0 = R.copy(), c.copy()
+    lr_r, lr_c = 1e-3, 2e-2
+    for k in range(1, 8):
+        O.adam_step(R, c, g, m, v, k, lr_r, lr_c, beta1=0.8, beta2=0.95, eps=0.0)
+        np.testing.assert_allclose(c, c0 - k * lr_c * np.sign(g[:, 3:]), atol=1e-13)
+        for q in range(3):
+            # the same increment k times about a fixed axis is one turn of k times its angle
+            np.testing.assert_allclose(R[q], O.expmap(-k * lr_r * np.sign(g[q, :3])) @ R0[q], atol=1e-12)
+
+
 def test_project_rotation_nearest():
     rng = np.random.default_rng(13)
     Q = O.expmap(rng.normal(size=3))
