@@ -1,14 +1,14 @@
-"""The oracle's pins catch plausible mistakes: each case plants one mistake in a copy of the
-oracle's C source (a transposed operand, a flipped sign, a dropped factor or term, a wrong
-normaliser, an inverted filter, a wrong rotation formula), builds the copy in a temporary
-folder and runs the pin tests against it in a fresh interpreter; at least one pin must fail.
-A control run of the unchanged copy must pass. The real oracle files are never touched.
-CPU only."""
+"""The oracle's pins catch plausible mistakes: each case copies the oracle package to a
+temporary folder, plants one mistake in the copy (a transposed operand, a flipped sign, a
+dropped factor, term or projection, a wrong normaliser, an inverted filter or selection, a
+wrong rotation formula) and runs the pin tests against the copy in a fresh interpreter; at
+least one pin must fail. A control run of the unchanged copy must pass. The real oracle files
+are never touched. CPU only."""
+import concurrent.futures as cf
 import os
+import shutil
 import subprocess
 import sys
-
-import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "epipolar.c")
@@ -42,32 +42,83 @@ MUTATIONS = [
      "const double bc1 = 1.0 - pow(beta1, (double)(step + 1));"),
 ]
 
-PINS = ["tests/test_oracle.py", "tests/test_oracle_focal.py"]
+# (module file, name, text, planted replacement) for the NumPy parts of the oracle
+PY_MUTATIONS = [
+    ("translation.py", "baseline direction sign", 'return -np.einsum("nba,nb->na", R[np.asarray(cam_j)], t)',
+     'return np.einsum("nba,nb->na", R[np.asarray(cam_j)], t)'),
+    ("translation.py", "L2 norm in place of L1", "term = np.abs(r).sum(1)", "term = np.sqrt((r * r).sum(1))"),
+    ("translation.py", "subgradient not projected", "g_u = (s - uh * (uh * s).sum(1, keepdims=True)) / nrm[:, None]",
+     "g_u = s / nrm[:, None]"),
+    ("translation.py", "merge keeps the worst run", "best = np.argmin(", "best = np.argmax("),
+    ("translation.py", "normalised by the largest norm", "return c / np.linalg.norm(c, axis=1).mean()",
+     "return c / np.linalg.norm(c, axis=1).max()"),
+    ("rotation.py", "connection blocks not transposed", "vals += [-w_pair * R_rel[p, a, b], -w_pair * R_rel[p, a, b]]",
+     "vals += [-w_pair * R_rel[p, a, b], -w_pair * R_rel[p, b, a]]"),
+    ("rotation.py", "second column not orthogonalised", "    y -= x * (x * y).sum(1, keepdims=True)\n", ""),
+    ("rotation.py", "third column sign", "z = np.cross(x, y)", "z = np.cross(y, x)"),
+    ("rotation.py", "6D second vector not orthogonalised", "u = a2 - b1 * (b1 * a2).sum(1, keepdims=True)\n    b2",
+     "u = a2\n    b2"),
+    ("rotation.py", "geodesic gradient sign", "dd = -0.5 / np.sqrt(1.0 - cc * cc)", "dd = 0.5 / np.sqrt(1.0 - cc * cc)"),
+    ("rotation.py", "relative rotation applied on the wrong side", "X = Rr @ R[ci]", "X = R[ci] @ Rr"),
+    ("focal.py", "scales of the two images swapped", "si = s[prob.cam_i][prob.pair_id][:, None]",
+     "si = s[prob.cam_j][prob.pair_id][:, None]"),
+    ("focal.py", "scale gradient not in log space", "return loss, g_pose, g_s * s", "return loss, g_pose, g_s"),
+    ("learned.py", "hidden ReLU dropped", "    h1 = np.maximum(z1, 0.0)\n", "    h1 = z1\n"),
+    ("learned.py", "cross-entropy gradient sign", "    dz3 = (p - y) / n\n    g = {\"W3\": h2.T @ dz3[:, None], \"b3\": np.array([dz3.sum()])}\n    dh2",
+     "    dz3 = (y - p) / n\n    g = {\"W3\": h2.T @ dz3[:, None], \"b3\": np.array([dz3.sum()])}\n    dh2"),
+    ("learned.py", "learned weight floor dropped", "w = p / np.maximum(abs_eps, delta)", "w = p / abs_eps"),
+]
+
+# pin files run against each mutated file
+PINS_FOR = {
+    "epipolar.c": ["tests/test_oracle.py", "tests/test_oracle_focal.py"],
+    "translation.py": ["tests/test_oracle_translation.py"],
+    "rotation.py": ["tests/test_oracle_rotation.py"],
+    "focal.py": ["tests/test_oracle_focal.py"],
+    "learned.py": ["tests/test_oracle_learned.py"],
+}
+ALL_PINS = ["tests/test_oracle.py", "tests/test_oracle_focal.py", "tests/test_oracle_translation.py",
+            "tests/test_oracle_rotation.py", "tests/test_oracle_learned.py"]
 
 
-def _run_pins(tmp_path, source: str) -> subprocess.CompletedProcess:
-    src = tmp_path / "epipolar.c"
-    src.write_text(source)
+def _run_pins(tmp_path, file: str, source: str, pins) -> subprocess.CompletedProcess:
+    """Run `pins` against a copy of the oracle package (in tmp_path) whose `file` holds `source`."""
+    dst = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), dst,
+                    ignore=shutil.ignore_patterns("__pycache__", "*.so", "*.tmp*"))
+    (dst / file).write_text(source)
     code = (
         "import sys\n"
-        f"sys.path.insert(0, {ROOT!r})\n"
+        f"sys.path[:0] = [{str(tmp_path)!r}, {ROOT!r}]\n"
         "import oracle\n"
-        f"oracle._SRC = {str(src)!r}\n"
-        f"oracle._LIB_PATH = {str(tmp_path / '_liboracle_copy.so')!r}\n"
-        "oracle._lib = None\n"
+        f"assert oracle.__file__.startswith({str(tmp_path)!r}), oracle.__file__\n"
         "import pytest\n"
-        f"sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', '-m', 'not gpu', *{PINS!r}]))\n")
-    return subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+        f"sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', '-m', 'not gpu', *{list(pins)!r}]))\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    return subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=900,
+                          env=env)
 
 
-def test_unchanged_copy_passes_the_pins(tmp_path):
-    r = _run_pins(tmp_path, open(SRC).read())
-    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+def test_planted_mistakes_fail_a_pin_and_the_unchanged_copy_passes(tmp_path):
+    cases = [("epipolar.c",) + m for m in MUTATIONS] + list(PY_MUTATIONS)
+    for file, name, text, _ in cases:
+        n = open(os.path.join(ROOT, "oracle", file)).read().count(text)
+        assert n == 1, f"pattern for {name!r} found {n} times in oracle/{file}"
+    # controls: the unchanged copy against every group of pins
+    cases = [(file, "control", "", "") for file in PINS_FOR] + cases
 
+    def run(k):
+        file, name, text, planted = cases[k]
+        source = open(os.path.join(ROOT, "oracle", file)).read()
+        if name != "control":
+            source = source.replace(text, planted)
+        work = tmp_path / f"case{k}"
+        work.mkdir()
+        r = _run_pins(work, file, source, PINS_FOR[file])
+        ok = r.returncode == 0 if name == "control" else (r.returncode == 1 and "FAILED" in r.stdout)
+        return f"{file}: {name}", ok, r.stdout[-1500:] + r.stderr[-1500:]
 
-@pytest.mark.parametrize("name,text,planted", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_planted_mistake_is_caught(tmp_path, name, text, planted):
-    source = open(SRC).read()
-    assert source.count(text) == 1, f"pattern for {name!r} not found once in the oracle source"
-    r = _run_pins(tmp_path, source.replace(text, planted))
-    assert r.returncode == 1 and "FAILED" in r.stdout, (name, r.stdout[-3000:], r.stderr[-2000:])
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        results = list(ex.map(run, range(len(cases))))
+    wrong = [(name, out) for name, ok, out in results if not ok]
+    assert not wrong, wrong

@@ -42,6 +42,17 @@ def test_initialisation_is_exact_on_noise_free_relative_rotations():
     assert np.abs(Ri - want).max() < 1e-9
 
 
+def test_initialisation_returns_rotations_on_noisy_input():
+    # with inconsistent relative rotations the least-squares columns are not orthogonal by
+    # themselves; the result must still be a proper rotation per camera, close to the truth
+    R, ci, cj, Rrel = _relative("sphere128", noise_deg=3.0)
+    Ri = G.initial_rotations(R.shape[0], ci, cj, Rrel)
+    eye = np.tile(np.eye(3), (R.shape[0], 1, 1))
+    np.testing.assert_allclose(np.einsum("nba,nbc->nac", Ri, Ri), eye, atol=1e-12)
+    np.testing.assert_allclose(np.linalg.det(Ri), 1.0, atol=1e-12)
+    assert O.rotation_error_deg(Ri, R).mean() < 3.0
+
+
 def test_six_d_round_trip_and_orthonormality():
     rng = np.random.default_rng(0)
     Rs = _random_rotations(20, rng)
