@@ -67,6 +67,13 @@ PY_MUTATIONS = [
     ("learned.py", "cross-entropy gradient sign", "    dz3 = (p - y) / n\n    g = {\"W3\": h2.T @ dz3[:, None], \"b3\": np.array([dz3.sum()])}\n    dh2",
      "    dz3 = (y - p) / n\n    g = {\"W3\": h2.T @ dz3[:, None], \"b3\": np.array([dz3.sum()])}\n    dh2"),
     ("learned.py", "learned weight floor dropped", "w = p / np.maximum(abs_eps, delta)", "w = p / abs_eps"),
+    ("learned.py", "pair-relative feature against the global mean", "f[:, 1] = le - mean_log[pair_id]",
+     "f[:, 1] = le - le.mean()"),
+    ("focal.py", "scale derivative keeps the homogeneous 1", "u1 = np.concatenate([prob.x1, np.zeros((prob.n_pp, 1))], 1)",
+     "u1 = np.concatenate([prob.x1, np.ones((prob.n_pp, 1))], 1)"),
+    ("translation.py", "camera loss counts only first images",
+     "s = np.bincount(cam_i, weights=term, minlength=n) + np.bincount(cam_j, weights=term, minlength=n)",
+     "s = 2 * np.bincount(cam_i, weights=term, minlength=n)"),
 ]
 
 # pin files run against each mutated file

@@ -85,6 +85,23 @@ def test_normalize_removes_translation_and_scale():
     np.testing.assert_allclose(T.normalize(3.0 * o + 7.0), n, atol=1e-13)
 
 
+def test_camera_losses_by_brute_force():
+    # a camera's loss is the mean L1 term over every pair it belongs to, as first or second image
+    R, C, ci, cj, t = _exact_directions()
+    oij = T.relative_directions(R, t, cj)
+    rng = np.random.default_rng(4)
+    o = C + 0.2 * rng.normal(size=C.shape)
+    terms = []
+    for i, j, d in zip(ci, cj, oij):
+        u = o[j] - o[i]
+        terms.append(np.abs(u / np.linalg.norm(u) - d).sum())
+    want = np.zeros(len(C))
+    for k in range(len(C)):
+        mine = [terms[p] for p in range(len(ci)) if ci[p] == k or cj[p] == k]
+        want[k] = np.mean(mine) if mine else 0.0
+    np.testing.assert_allclose(T.camera_losses(o, ci, cj, oij), want, rtol=1e-13)
+
+
 def test_merge_takes_each_camera_from_its_best_run():
     R, C, ci, cj, t = _exact_directions()
     oij = T.relative_directions(R, t, cj)
