@@ -356,7 +356,10 @@ def test_fp16_centroid_rule_brute_force():
     for x, d, cam in ((x1, d1, prob.cam_i), (x2, d2, prob.cam_j)):
         off = x.astype(np.float32) - cen[cam[prob.pair_id]]
         ulp = np.spacing(np.abs(off).astype(np.float16)).astype(np.float64)
-        assert (np.abs(d - cen[cam[prob.pair_id]].astype(np.float64) - off) <= 0.5 * ulp + 1e-12).all()
+        stored = d - cen[cam[prob.pair_id]].astype(np.float64)
+        assert (np.abs(stored - off) <= 0.5 * ulp + 1e-12).all()
+        # and the stored offsets are FP16 numbers (the storage is FP16, not merely close to it)
+        assert np.array_equal(stored.astype(np.float16).astype(np.float64), stored)
 
 
 def test_fp16_weight_quantization():

@@ -44,6 +44,13 @@ MUTATIONS = [
 
 # (module file, name, text, planted replacement) for the NumPy parts of the oracle
 PY_MUTATIONS = [
+    ("__init__.py", "threshold floor ignored", "return max(tau_min, tau0 * factor ** r)", "return tau0 * factor ** r"),
+    ("__init__.py", "quadratic-form vector flattened column-major", 'v = np.einsum("pr,pc->prc", b, a).reshape(-1, 9)',
+     'v = np.einsum("pr,pc->pcr", b, a).reshape(-1, 9)'),
+    ("__init__.py", "offsets kept in FP32", "o1 = (x1 - cen[ci]).astype(np.float16)", "o1 = (x1 - cen[ci])"),
+    ("__init__.py", "weight scale not applied", "q = (np.asarray(w, dtype=np.float32) * s).astype(np.float16)",
+     "q = (np.asarray(w, dtype=np.float32)).astype(np.float16) * s"),
+    ("__init__.py", "gauge rotation transposed", "return _geodesic_deg(Rg, Re @ Q)", "return _geodesic_deg(Rg, Re @ Q.T)"),
     ("translation.py", "baseline direction sign", 'return -np.einsum("nba,nb->na", R[np.asarray(cam_j)], t)',
      'return np.einsum("nba,nb->na", R[np.asarray(cam_j)], t)'),
     ("translation.py", "L2 norm in place of L1", "term = np.abs(r).sum(1)", "term = np.sqrt((r * r).sum(1))"),
@@ -79,6 +86,7 @@ PY_MUTATIONS = [
 # pin files run against each mutated file
 PINS_FOR = {
     "epipolar.c": ["tests/test_oracle.py", "tests/test_oracle_focal.py"],
+    "__init__.py": ["tests/test_oracle.py"],
     "translation.py": ["tests/test_oracle_translation.py"],
     "rotation.py": ["tests/test_oracle_rotation.py"],
     "focal.py": ["tests/test_oracle_focal.py"],
