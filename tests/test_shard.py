@@ -1,6 +1,7 @@
-"""Sharding across processes, tested without a GPU: the partition, and world-size-2 gloo
-ranks that each compute their shard with the oracle, all-reduce, and take the replicated
-optimiser step; the result must equal the single-process oracle on the whole problem."""
+"""Sharding across processes, tested without a GPU: the partition, and gloo ranks (world
+sizes 2 and 3) that each compute their shard with the oracle, all-reduce, and take the
+replicated optimiser step; the result must equal the single-process oracle on the whole
+problem."""
 import os
 import socket
 
@@ -97,7 +98,8 @@ def _rank(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def test_gloo_world_size_2_matches_single_process():
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_match_single_process(world):
     import oracle as O
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -105,16 +107,17 @@ def test_gloo_world_size_2_matches_single_process():
     ctx = mp.get_context("spawn")
     manager = ctx.Manager()
     out = manager.dict()
-    mp.start_processes(_rank, args=(2, port, out), nprocs=2, join=True, start_method="spawn")
+    mp.start_processes(_rank, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
     prob, R0, c0 = _problem()
     l_full, g_full = O.loss_grad(prob, R0, c0, np.ones(prob.n_pp))
-    for r in (0, 1):
+    for r in range(world):
         buf = out[r][0]
         np.testing.assert_allclose(buf[:-1].reshape(-1, 6), g_full, rtol=1e-10, atol=1e-13 * np.abs(g_full).max())
         assert buf[-1] == pytest.approx(l_full, rel=1e-12)
     # replicas stayed identical
-    np.testing.assert_array_equal(out[0][1], out[1][1])
-    np.testing.assert_array_equal(out[0][2], out[1][2])
+    for r in range(1, world):
+        np.testing.assert_array_equal(out[0][1], out[r][1])
+        np.testing.assert_array_equal(out[0][2], out[r][2])
     # and equal the single-process loop (same rounds)
     R, c = R0.copy(), c0.copy()
     m, v = np.zeros((prob.n_cams, 6)), np.zeros((prob.n_cams, 6))
