@@ -78,6 +78,12 @@ PY_MUTATIONS = [
      "f[:, 1] = le - le.mean()"),
     ("focal.py", "scale derivative keeps the homogeneous 1", "u1 = np.concatenate([prob.x1, np.zeros((prob.n_pp, 1))], 1)",
      "u1 = np.concatenate([prob.x1, np.ones((prob.n_pp, 1))], 1)"),
+    ("focal_vote.py", "intrinsics applied inverted", "s1 = np.stack([f1, f1, np.ones_like(f1)], axis=1)",
+     "s1 = np.stack([1.0 / f1, 1.0 / f1, np.ones_like(f1)], axis=1)"),
+    ("focal_vote.py", "ratio of the two smallest singular values", "r = sv[:, 0] / sv[:, 1]", "r = sv[:, 1] / sv[:, 2]"),
+    ("focal_vote.py", "temperature sign", "out[c] = np.exp((1.0 - r) / tau).sum()", "out[c] = np.exp((r - 1.0) / tau).sum()"),
+    ("focal_vote.py", "known focal length read from the other side", "f1 = np.where(k1 > 0, k1, f)",
+     "f1 = np.where(k2 > 0, k2, f)"),
     ("translation.py", "camera loss counts only first images",
      "s = np.bincount(cam_i, weights=term, minlength=n) + np.bincount(cam_j, weights=term, minlength=n)",
      "s = 2 * np.bincount(cam_i, weights=term, minlength=n)"),
@@ -91,9 +97,10 @@ PINS_FOR = {
     "rotation.py": ["tests/test_oracle_rotation.py"],
     "focal.py": ["tests/test_oracle_focal.py"],
     "learned.py": ["tests/test_oracle_learned.py"],
+    "focal_vote.py": ["tests/test_oracle_focal_vote.py"],
 }
 ALL_PINS = ["tests/test_oracle.py", "tests/test_oracle_focal.py", "tests/test_oracle_translation.py",
-            "tests/test_oracle_rotation.py", "tests/test_oracle_learned.py"]
+            "tests/test_oracle_rotation.py", "tests/test_oracle_learned.py", "tests/test_oracle_focal_vote.py"]
 
 
 def _run_pins(tmp_path, file: str, source: str, pins) -> subprocess.CompletedProcess:
