@@ -203,7 +203,10 @@ FM_API fm_status fm_last_loss(fm_problem *p, double *loss);
 /*
  * One optimiser step with a gradient computed elsewhere (for example the sum of the gradients
  * of a problem's shards on several processes): grad is n_cams x 6 FP64, host, or device when
- * on_device is 1. Same update as one fm_step iteration. Synchronises.
+ * on_device is 1. Same update as one fm_step iteration. With a host gradient it synchronises;
+ * with a device gradient it only enqueues, ordered after the work queued on the caller's stream
+ * (so a collective that wrote the gradient on that stream needs no host wait), and a non-finite
+ * device gradient surfaces as FM_EDEGENERATE at the next synchronising call.
  */
 FM_API fm_status fm_apply_gradient(fm_problem *p, const double *grad, int32_t on_device);
 
@@ -241,6 +244,30 @@ FM_API fm_status fm_get_focal_scales(fm_problem *p, double *s);
 FM_API fm_status fm_set_focal_scales(fm_problem *p, const double *s);
 /* d loss / d rho_k (host FP64 n_cams) of the last fm_loss_grad or optimiser step. Synchronises. */
 FM_API fm_status fm_get_focal_gradient(fm_problem *p, double *g);
+
+/* ---- focal-length vote (Sec. "Intrinsics Estimation", Eq. fastmap-focal-vote) -------------------
+ * A 3x3 matrix is an essential matrix exactly when its two largest singular values are equal
+ * (and the third is zero). For fundamental matrices F_i of image pairs and a candidate focal
+ * length f, E_i = K_2^T F_i K_1 with K = diag(f, f, 1) (principal point at the image centre) and
+ *   v(f) = sum_i exp((1 - lambda_1^(i) / lambda_2^(i)) / tau)
+ * scores the candidate; the estimate is the candidate with the largest vote (chosen by the
+ * caller from the votes). A pair side whose focal length is already known uses that value
+ * instead of the candidate (the paper's procedure for several cameras).
+ *   F: n_pairs x 9 FP64 host, row-major, x2^T F x1 = 0 with x in pixels from the image centre
+ *      (each F is normalised to unit norm internally; the ratio is scale-free); finite, non-zero.
+ *   f1_known, f2_known: n_pairs FP64 host known focal length of side 1 / side 2 of each pair,
+ *      0 = use the candidate; either may be NULL (the candidate on that side for every pair).
+ *   cand: n_cand FP64 host candidates (> 0); tau > 0 the temperature.
+ *   votes: n_cand FP64 host output. elapsed_ms: if not NULL, the device time of the vote
+ *      kernels (CUDA events on `stream`).
+ * Numerics: FP32 per (candidate, pair) term (E, E^T E, four cyclic Jacobi sweeps for its
+ * eigenvalues), per-block FP32 sums in a fixed order, FP64 total per candidate: bit-reproducible.
+ * A pair with lambda_2 = 0 contributes 0. Allocates and frees its device buffers on `stream`
+ * (a cudaStream_t, NULL = legacy default) and synchronises it. FM_EINVAL on bad arguments.
+ */
+FM_API fm_status fm_focal_vote(int32_t n_pairs, const double *F, const double *f1_known,
+                               const double *f2_known, int32_t n_cand, const double *cand, double tau,
+                               double *votes, float *elapsed_ms, void *stream);
 
 /* ---- pre-aggregated quadratic form (Eq. epipolar-objective-l2 with the IRLS weights) ---------
  * With the weights held fixed, the objective of image pair n is quadratic in the 9 entries
@@ -449,15 +476,21 @@ FM_API fm_status fm_rotation_set_params(fm_rotation *rp, const double *a6);
  * Limits: 2 <= n_cams <= 4096, 1 <= n_pairs <= 32768, n_pairs <= n_pp <= 2^26; larger
  * problems return FM_EINVAL (use fm_create_problem for them).
  *
- * Intermediates live in one fixed 10.7 MiB __device__ array of the library, held on every
+ * Intermediates live in one fixed 10.9 MiB __device__ array of the library, held on every
  * device that loads it until the process exits. The first call on a device looks up the
  * array's device address with that device current; make that first call before any stream
  * capture. Every call shares the array, so calls that overlap on the GPU (other streams,
  * other host threads on the same device) race and must be serialised by the caller.
  * Runs on `stream` (a cudaStream_t, NULL = legacy default) and synchronises it before
- * returning. Invalid device data (offsets not rising, camera index out of range,
- * cam_i == cam_j) returns FM_EINVAL; a zero-length relative translation or a non-finite
- * result returns FM_EDEGENERATE.
+ * returning. Invalid device data returns FM_EINVAL with nothing written to d_loss/d_grad
+ * that the caller may rely on: offsets not rising, a camera index out of range, cam_i ==
+ * cam_j, a keypoint coordinate that is not finite or exceeds 8 in magnitude, a weight that is
+ * negative or not finite (the same input rules as fm_create_problem and fm_set_weights; no
+ * upper bound is imposed on the weights here, since no IRLS floor delta is given). A
+ * zero-length relative translation or a non-finite result returns FM_EDEGENERATE.
+ * Cost: besides the pass over the point pairs, O(n_pairs + n_cams) work to build each
+ * camera's list of image pairs plus O(d_k^2) for camera k of degree d_k to put its list into
+ * pair order.
  */
 FM_API fm_status fm_loss_grad_noalloc(int32_t n_cams, const double *d_R, const double *d_c,
                                       int32_t n_pairs, const int32_t *d_cam_i,

@@ -32,7 +32,7 @@ EXPORTED = [
     "fm_translation_set_learning_rate", "fm_translation_get_centres", "fm_translation_set_centres",
     "fm_rotation_default_options", "fm_rotation_create", "fm_rotation_destroy", "fm_rotation_initialize",
     "fm_rotation_loss_grad", "fm_rotation_step", "fm_rotation_set_learning_rate", "fm_rotation_get_rotations",
-    "fm_rotation_get_params", "fm_rotation_set_rotations", "fm_rotation_set_params",
+    "fm_rotation_get_params", "fm_rotation_set_rotations", "fm_rotation_set_params", "fm_focal_vote",
 ]
 
 
@@ -138,6 +138,7 @@ def load_library(path: str = LIB_PATH):
         "fm_rotation_get_params": (I32, [P, P]),
         "fm_rotation_set_rotations": (I32, [P, P]),
         "fm_rotation_set_params": (I32, [P, P]),
+        "fm_focal_vote": (I32, [I32, P, P, P, I32, P, D, P, P, P]),
         "fm_status_string": (ctypes.c_char_p, [I32]),
         "fm_last_error": (ctypes.c_char_p, []),
     }
@@ -600,6 +601,27 @@ class Rotation:
     def set_params(self, a6):
         a6 = np.ascontiguousarray(_host(a6, np.float64).reshape(self.n_cams, 6))
         _check(load_library().fm_rotation_set_params(self._h, _ptr(a6)))
+
+
+def focal_vote(F, candidates, tau: float, f1_known=None, f2_known=None, timed: bool = False, stream=None):
+    """Votes v(f) of the candidate focal lengths (fm_focal_vote; Sec. "Intrinsics Estimation").
+    F: (B, 3, 3) fundamental matrices in pixels from the image centre; f1_known / f2_known: (B,)
+    known focal length of each pair side, 0 where the candidate is used. Returns the votes
+    (FP64 array), and with timed=True also the kernels' device time in ms."""
+    Fh = np.ascontiguousarray(_host(F, np.float64).reshape(-1, 9))
+    ch = np.ascontiguousarray(_host(candidates, np.float64).reshape(-1))
+    k1 = None if f1_known is None else np.ascontiguousarray(_host(f1_known, np.float64).reshape(-1))
+    k2 = None if f2_known is None else np.ascontiguousarray(_host(f2_known, np.float64).reshape(-1))
+    for k in (k1, k2):
+        if k is not None and k.shape[0] != Fh.shape[0]:
+            raise ValueError("known focal lengths need one value per pair")
+    out = np.empty(ch.shape[0], np.float64)
+    ms = ctypes.c_float()
+    _check(load_library().fm_focal_vote(Fh.shape[0], _ptr(Fh), None if k1 is None else _ptr(k1),
+                                        None if k2 is None else _ptr(k2), ch.shape[0], _ptr(ch), float(tau),
+                                        _ptr(out), ctypes.byref(ms) if timed else None,
+                                        stream if stream is not None else _current_stream()))
+    return (out, ms.value) if timed else out
 
 
 class Mlp:
