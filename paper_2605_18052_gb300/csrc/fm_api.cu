@@ -833,7 +833,7 @@ FM_API fm_status fm_apply_gradient(fm_problem *p, const double *grad, int32_t on
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->s));
     launch_apply_gradient(p->d, p->s);
     FM_CUDA(cudaGetLastError());
-    FM_CUDA(cudaStreamSynchronize(p->s));
+    if (!on_device) FM_CUDA(cudaStreamSynchronize(p->s));   // the host buffer may be reused at once
     FM_CUDA(join_out(p));
     return FM_OK;
 }

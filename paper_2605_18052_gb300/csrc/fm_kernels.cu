@@ -509,7 +509,9 @@ __global__ void k_apply_gradient(DevProblem d) {
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             const size_t o = (size_t)kc * 6 + q;
-            const float gq = (float)d.grad[o];
+            const double g64 = d.grad[o];
+            if (!isfinite(g64)) atomicOr(d.err, ERR_NONFINITE);
+            const float gq = (float)g64;
             mo[q] = b1 * d.m[o] + (1.f - b1) * gq;
             vo[q] = b2 * d.v[o] + (1.f - b2) * gq * gq;
             dl[q] = (double)(-(q < 3 ? lr_r : lr_c) * (mo[q] / bc1) / (sqrtf(vo[q] / bc2) + eps));

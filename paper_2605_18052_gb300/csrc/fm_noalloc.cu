@@ -33,8 +33,10 @@ constexpr size_t OFF_SLOTS = OFF_RANGE + al256(sizeof(int) * NA_MAX_RANGES);
 constexpr size_t OFF_PG = OFF_SLOTS + al256(sizeof(float) * SLOT * ((size_t)NA_MAX_PAIRS + NA_MAX_RANGES));
 constexpr size_t OFF_CAMOFF = OFF_PG + al256(sizeof(float) * PG * NA_MAX_PAIRS);
 constexpr size_t OFF_CAMENT = OFF_CAMOFF + al256(sizeof(int) * (NA_MAX_CAMS + 1));
-constexpr size_t OFF_ERR = OFF_CAMENT + al256(sizeof(int) * 2 * NA_MAX_PAIRS);
-constexpr size_t NA_SCRATCH_BYTES = OFF_ERR + 256;   // about 10.7 MiB
+constexpr size_t OFF_CAMTMP = OFF_CAMENT + al256(sizeof(int) * 2 * NA_MAX_PAIRS);
+constexpr size_t OFF_CURSOR = OFF_CAMTMP + al256(sizeof(int) * 2 * NA_MAX_PAIRS);
+constexpr size_t OFF_ERR = OFF_CURSOR + al256(sizeof(int) * NA_MAX_CAMS);
+constexpr size_t NA_SCRATCH_BYTES = OFF_ERR + 256;   // about 10.9 MiB
 
 // Host code must not use this name as an address: it is a host-side stand-in. The device
 // address comes from cudaGetSymbolAddress (scratch_base below).
@@ -73,18 +75,16 @@ __global__ void k_na_check(const int *pair_off, const int *cam_i, const int *cam
     if (!ok) atomicOr(err, ERR_PAIR_RANGE);
 }
 
-// ---- camera -> (pair, role) lists, in pair order: one warp per camera ------------------------
-__global__ void k_na_cam_count(const int *cam_i, const int *cam_j, int n_pairs, int n_cams, int *cnt) {
-    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (k >= n_cams) return;
-    int c = 0;
-    for (int base = 0; base < n_pairs; base += 32) {
-        const int n = base + lane;
-        const bool hit = n < n_pairs && (cam_i[n] == k || cam_j[n] == k);
-        c += __popc(__ballot_sync(0xffffffffu, hit));
-    }
-    if (lane == 0) cnt[k + 1] = c;
+// ---- camera -> (pair, role) lists, in pair order --------------------------------------------
+// O(n_pairs) counting and filling with atomics, then every camera's list is put into pair order
+// (the order in which the per-camera gradient sums are taken, so results are reproducible):
+// each entry's rank is the number of smaller entries of the same camera, O(sum of squared
+// camera degrees) in all.
+__global__ void k_na_cam_count(const int *cam_i, const int *cam_j, int n_pairs, int *cnt) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_pairs) return;
+    atomicAdd(&cnt[cam_i[n] + 1], 1);
+    atomicAdd(&cnt[cam_j[n] + 1], 1);
 }
 
 __global__ void k_na_cam_scan(int *off, int n_cams) {  // one block: off[0] = 0, inclusive scan
@@ -111,19 +111,26 @@ __global__ void k_na_cam_scan(int *off, int n_cams) {  // one block: off[0] = 0,
     if (threadIdx.x == 0) off[0] = 0;
 }
 
-__global__ void k_na_cam_fill(const int *cam_i, const int *cam_j, int n_pairs, int n_cams,
-                              const int *off, int *ent) {
+__global__ void k_na_cam_fill(const int *cam_i, const int *cam_j, int n_pairs, const int *off, int *cursor,
+                              int *tmp) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_pairs) return;
+    const int i = cam_i[n], j = cam_j[n];
+    tmp[off[i] + atomicAdd(&cursor[i], 1)] = 2 * n;
+    tmp[off[j] + atomicAdd(&cursor[j], 1)] = 2 * n + 1;
+}
+
+// one warp per camera: entry e goes to position off[k] + #{entries of k smaller than e}
+__global__ void k_na_cam_order(const int *off, const int *tmp, int n_cams, int *ent) {
     const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (k >= n_cams) return;
-    int pos = off[k];
-    for (int base = 0; base < n_pairs; base += 32) {
-        const int n = base + lane;
-        const bool hi = n < n_pairs && cam_i[n] == k;
-        const bool hj = n < n_pairs && cam_j[n] == k;
-        const unsigned m = __ballot_sync(0xffffffffu, hi || hj);
-        if (hi || hj) ent[pos + __popc(m & ((1u << lane) - 1u))] = 2 * n + (hj ? 1 : 0);
-        pos += __popc(m);
+    const int b = off[k], e = off[k + 1];
+    for (int a = b + lane; a < e; a += 32) {
+        const int v = tmp[a];
+        int rank = 0;
+        for (int c = b; c < e; ++c) rank += tmp[c] < v ? 1 : 0;
+        ent[b + rank] = v;
     }
 }
 
@@ -166,6 +173,16 @@ __global__ void __launch_bounds__(256) k_na_stream(DevProblem d, const float4 *k
         if (q < p_end) {
             v = kp[q];
             wq = w ? w[q] : 1.f;
+            // the same input rules as fm_create_problem / fm_set_weights: finite coordinates
+            // of magnitude <= 8, finite non-negative weights (the point pair is then skipped)
+            const bool coord_ok = fabsf(v.x) <= COORD_LIMIT && fabsf(v.y) <= COORD_LIMIT &&
+                                  fabsf(v.z) <= COORD_LIMIT && fabsf(v.w) <= COORD_LIMIT;
+            const bool w_ok = wq >= 0.f && wq <= 3.0e38f;
+            if (!coord_ok || !w_ok) {
+                atomicOr(d.err, coord_ok ? ERR_WEIGHT : ERR_COORD);
+                v = make_float4(0.f, 0.f, 0.f, 0.f);
+                wq = 0.f;
+            }
         }
         int64_t lo = gb;
         const int64_t g_end = min(gb + 32, p_end);
@@ -290,12 +307,16 @@ extern "C" FM_API fm_status fm_loss_grad_noalloc(int32_t n_cams, const double *d
         return na_fail(FM_EINVAL, "fm_loss_grad_noalloc: pair_off must rise strictly from 0 to n_pp "
                                   "and camera indices must be valid with cam_i != cam_j");
 
+    int *cam_tmp = reinterpret_cast<int *>(base + OFF_CAMTMP);
+    int *cursor = reinterpret_cast<int *>(base + OFF_CURSOR);
+    NA_CUDA(cudaMemsetAsync(d.cam_off, 0, sizeof(int) * (n_cams + 1), s));
+    NA_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * n_cams, s));
     launch_cam_prep(d, s);
     launch_range_pairs(d.pair_off, n_pairs, d.n_ranges, d.range_pair, s);
-    k_na_cam_count<<<(n_cams + 7) / 8, 256, 0, s>>>(d.cam_i, d.cam_j, n_pairs, n_cams, d.cam_off);
+    k_na_cam_count<<<(n_pairs + 255) / 256, 256, 0, s>>>(d.cam_i, d.cam_j, n_pairs, d.cam_off);
     k_na_cam_scan<<<1, 1024, 0, s>>>(d.cam_off, n_cams);
-    k_na_cam_fill<<<(n_cams + 7) / 8, 256, 0, s>>>(d.cam_i, d.cam_j, n_pairs, n_cams, d.cam_off,
-                                                  d.cam_ent);
+    k_na_cam_fill<<<(n_pairs + 255) / 256, 256, 0, s>>>(d.cam_i, d.cam_j, n_pairs, d.cam_off, cursor, cam_tmp);
+    k_na_cam_order<<<(n_cams + 7) / 8, 256, 0, s>>>(d.cam_off, cam_tmp, n_cams, d.cam_ent);
     launch_pair_setup(d, s);
     k_na_stream<<<(d.n_ranges + 7) / 8, 256, 0, s>>>(d, reinterpret_cast<const float4 *>(d_kp),
                                                       loss == FM_LOSS_IRLS ? d_w : nullptr);
@@ -304,6 +325,10 @@ extern "C" FM_API fm_status fm_loss_grad_noalloc(int32_t n_cams, const double *d
     NA_CUDA(cudaGetLastError());
     NA_CUDA(cudaMemcpyAsync(&err, d.err, sizeof err, cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
+    if (err & (ERR_COORD | ERR_WEIGHT))
+        return na_fail(FM_EINVAL, (err & ERR_COORD)
+                                      ? "fm_loss_grad_noalloc: keypoint coordinates must be finite with magnitude <= 8"
+                                      : "fm_loss_grad_noalloc: weights must be finite and >= 0");
     if (err & (ERR_DEGENERATE | ERR_NONFINITE))
         return na_fail(FM_EDEGENERATE, "fm_loss_grad_noalloc: zero-length relative translation or "
                                        "non-finite loss/gradient");

@@ -98,15 +98,24 @@ struct QuadBody {
     }
 };
 
+// groups in flight per warp and resident CTAs per SM of the accumulation pass (the 46 running
+// sums leave room for few of either)
+#ifndef FM_QUAD_UNROLL
+#define FM_QUAD_UNROLL 4
+#endif
+#ifndef FM_QUAD_MIN_CTAS
+#define FM_QUAD_MIN_CTAS 2
+#endif
+
 template <int STORE, bool REWEIGHT>
-__global__ void __launch_bounds__(CTA_WARPS * 32, 2) k_quad_accumulate(DevProblem d, float tau) {
+__global__ void __launch_bounds__(CTA_WARPS * 32, FM_QUAD_MIN_CTAS) k_quad_accumulate(DevProblem d, float tau) {
     __shared__ unsigned cta_kept;
     if (threadIdx.x == 0) cta_kept = 0;
     __syncthreads();
     const int r = blockIdx.x * CTA_WARPS + (threadIdx.x >> 5);
     if (r < d.n_ranges) {
         QuadBody<STORE, REWEIGHT> body(d, tau);
-        walk_range<STORE, !REWEIGHT>(d, r, threadIdx.x & 31, body);
+        walk_range<STORE, !REWEIGHT, QuadBody<STORE, REWEIGHT>, FM_QUAD_UNROLL>(d, r, threadIdx.x & 31, body);
         if (REWEIGHT) {
             unsigned k = body.kept;
 #pragma unroll

@@ -145,12 +145,12 @@ __device__ __forceinline__ float irls_weight(float a, float delta) { return __fd
 // contiguous 512 B block. The image pair changes only at sorted boundaries: a group that lies
 // inside the current pair takes the fast path; a group that crosses a boundary is processed in
 // passes, one pass per image pair it meets, and `body.segment_end` closes each finished pair.
-template <int STORE, bool NEED_W, class Body>
+// U groups are loaded before any is processed (loads in flight per warp).
+template <int STORE, bool NEED_W, class Body, int U = 4>
 __device__ __forceinline__ void walk_range(const DevProblem &d, int r, int lane, Body &body) {
     using F = Fmt<STORE>;
     constexpr int PPL = F::PPL;
     constexpr int GROUP = 32 * PPL;
-    constexpr int U = 4;
     static_assert(WR % (U * GROUP) == 0, "range must be whole unrolled groups");
     const int64_t p_begin = (int64_t)r * WR;
     const int64_t p_end = min(p_begin + (int64_t)WR, d.n_pp);

@@ -8,8 +8,16 @@ ranges; one all-reduce (sum) of the N x 6 gradient and the loss per iteration gi
 process the full gradient, and the replicated optimiser step keeps the replicas identical.
 The reweighting passes are local (a point pair's weight depends on its own residual only).
 
-Host control flow only; the per-rank compute comes from a backend (the GPU problem of this
-library, `GpuShard`), the collective from torch.distributed.
+Host control flow only; the per-rank compute comes from a backend, the collective from
+torch.distributed. Two data planes:
+  * host (`GpuShard`): the gradient comes to the host each iteration and is all-reduced as a
+    CPU tensor (gloo);
+  * device (`DeviceGpuShard`): the library writes the loss and gradient into one device buffer
+    (fm_loss_grad_device), the collective sums that buffer in place on the device (NCCL), and
+    the library takes the optimiser step from it (fm_apply_gradient on device memory). All three
+    are ordered on the current CUDA stream; nothing waits on the host inside an iteration.
+A backend that has `new_buffer`, `loss_grad_into` and `apply_gradient_from` gets the device
+plane.
 """
 from __future__ import annotations
 
@@ -63,6 +71,20 @@ class GpuShard:
         self.p.set_learning_rate(lr_rot, lr_c)
 
 
+class DeviceGpuShard(GpuShard):
+    """Backend with the device data plane: gradient and loss stay in device memory."""
+
+    def new_buffer(self):
+        """[n_cams * 6 gradient entries, loss] as one float64 tensor on the problem's device."""
+        return torch.zeros(self.p.n_cams * 6 + 1, dtype=torch.float64, device="cuda")
+
+    def loss_grad_into(self, buf):
+        self.p.loss_grad_device(buf[-1:], buf[:-1])
+
+    def apply_gradient_from(self, buf):
+        self.p.apply_gradient(buf[:-1].view(-1, 6))
+
+
 class ShardedAdjustment:
     """The IRLS loop over a sharded problem: local reweighting, per-iteration all-reduce of
     the gradient and the loss, replicated optimiser step."""
@@ -70,12 +92,24 @@ class ShardedAdjustment:
     def __init__(self, backend, group=None):
         self.b = backend
         self.group = group
+        self.device_plane = all(hasattr(backend, a) for a in ("new_buffer", "loss_grad_into", "apply_gradient_from"))
+        self.buf = backend.new_buffer() if self.device_plane else None
 
-    def iteration(self) -> float:
-        loss, grad = self.b.loss_grad()
-        buf = torch.from_numpy(np.concatenate([np.asarray(grad, np.float64).ravel(), [loss]]))
+    def _all_reduce(self, buf):
         if dist.is_available() and dist.is_initialized():
             dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=self.group)
+
+    def iteration(self):
+        """One iteration; returns the total loss (a float on the host plane, a one-element
+        tensor on the device plane, read without waiting only when the caller converts it)."""
+        if self.device_plane:
+            self.b.loss_grad_into(self.buf)
+            self._all_reduce(self.buf)
+            self.b.apply_gradient_from(self.buf)
+            return self.buf[-1:]
+        loss, grad = self.b.loss_grad()
+        buf = torch.from_numpy(np.concatenate([np.asarray(grad, np.float64).ravel(), [loss]]))
+        self._all_reduce(buf)
         total = buf.numpy()
         self.b.apply_gradient(total[:-1].reshape(-1, 6))
         return float(total[-1])
@@ -86,7 +120,7 @@ class ShardedAdjustment:
         loss = float("nan")
         for _ in range(iters):
             loss = self.iteration()
-        return loss
+        return float(loss[0]) if self.device_plane and iters > 0 else float(loss)
 
     def run(self, schedule) -> float:
         loss = float("nan")

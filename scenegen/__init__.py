@@ -88,6 +88,14 @@ class Scene:
 #               evaluated on seeds outside the training seeds 1000-1199).
 #   traj4000  : 4,000 cameras, 2M points, 25 neighbours (~5e4 pairs), Pareto(1.5) counts
 #               capped at 50k (~1.5e8 point pairs), 25% outliers, 1.5 px.
+#   loop1000  : 1,000 cameras along a random smooth closed trajectory that circles a 500k-point
+#               cloud in 5 laps at changing heights (every lap closes a loop and neighbouring
+#               laps revisit the same views), looking inward; 20 neighbours per camera: 8 along
+#               the path and 12 nearest views elsewhere on it (~1e4 pairs), log-normal counts
+#               (~5e7 point pairs), 20% outliers, 1 px.
+#   loop1000_o30 : loop1000 with 30% outliers (learned-weight evaluation scene).
+#   loop4000  : loop1000's layout at the size of traj4000 (4,000 cameras, 2M points,
+#               25 neighbours, Pareto(1.5) counts capped at 50k, 25% outliers, 1.5 px).
 CONFIGS = {
     "ring16": dict(kind="ring", n_cams=16, n_pts=2000, sigma_px=0.5, outlier=0.10,
                    keep=0.5, iters=200),
@@ -104,6 +112,12 @@ CONFIGS = {
     "traj4000": dict(kind="trajectory", n_cams=4000, n_pts=2_000_000, sigma_px=1.5,
                      outlier=0.25, knn=25, counts=("pareto", 1.5, 1100.0, 50_000),
                      spacing=0.1, depth=(4.0, 16.0), iters=300),
+    "loop1000": dict(kind="loop", n_cams=1000, n_pts=500_000, sigma_px=1.0, outlier=0.20,
+                     knn=20, path_nb=4, laps=5, counts=("lognormal", 3900.0, 0.9, 20_000), iters=300),
+    "loop1000_o30": dict(kind="loop", n_cams=1000, n_pts=500_000, sigma_px=1.0, outlier=0.30,
+                         knn=20, path_nb=4, laps=5, counts=("lognormal", 3900.0, 0.9, 20_000), iters=300),
+    "loop4000": dict(kind="loop", n_cams=4000, n_pts=2_000_000, sigma_px=1.5, outlier=0.25,
+                     knn=25, path_nb=5, laps=10, counts=("pareto", 1.5, 1100.0, 50_000), iters=300),
 }
 
 
@@ -215,6 +229,53 @@ def _cams_sphere(n: int, g, device, radius: float, jitter_deg: float):
     R = _look_rotation(-C, up)
     jit = (torch.rand(n, 3, dtype=F64, generator=g, device=device) * 2 - 1) * math.radians(jitter_deg)
     return rotation_exp(jit) @ R, C
+
+
+def _cams_loop(n: int, laps: int, g, device, radius: float = 3.0, jitter_deg: float = 10.0):
+    """Cameras along a random smooth closed trajectory around the origin, looking inward.
+
+    The path winds `laps` times around the vertical axis; its elevation follows one slow
+    cosine over the whole path (so later laps pass over the heights of earlier ones) and its
+    radius and elevation carry random low-order Fourier terms that are periodic over the whole
+    path, so the curve is smooth and closes on itself.
+    """
+    s = (torch.arange(n, dtype=F64, device=device) + 0.5) / n          # path parameter in [0, 1)
+    theta = 2 * math.pi * laps * s
+    phase = 2 * math.pi * float(torch.rand(1, dtype=F64, generator=g, device=device))
+    elev = math.radians(35.0) * torch.cos(2 * math.pi * s + phase)
+    rad = torch.full_like(s, radius)
+    for k in range(1, 4):   # wobble: closed (periodic in s), decaying with the order
+        a = torch.randn(4, dtype=F64, generator=g, device=device) / k
+        arg = 2 * math.pi * (k * (laps + 1)) * s
+        rad = rad + radius * 0.06 * (a[0] * torch.cos(arg) + a[1] * torch.sin(arg))
+        elev = elev + math.radians(4.0) * (a[2] * torch.cos(arg) + a[3] * torch.sin(arg))
+    C = torch.stack([rad * torch.cos(elev) * torch.cos(theta), rad * torch.cos(elev) * torch.sin(theta),
+                     rad * torch.sin(elev)], -1)
+    up = torch.tensor([0.0, 0.0, 1.0], dtype=F64, device=device).expand(n, 3)
+    R = _look_rotation(-C, up)
+    jit = (torch.rand(n, 3, dtype=F64, generator=g, device=device) * 2 - 1) * math.radians(jitter_deg)
+    return rotation_exp(jit) @ R, C
+
+
+def _loop_pairs(C: torch.Tensor, path_nb: int, k_far: int, far_steps: int):
+    """Pairs of a closed path: every camera with its `path_nb` neighbours on each side along
+    the path (wrapping around), and with its `k_far` nearest cameras that are more than
+    `far_steps` steps away along the path (the views of other laps: revisits)."""
+    n = C.shape[0]
+    dev = C.device
+    idx = torch.arange(n, device=dev)
+    near = (idx[:, None] + torch.arange(1, path_nb + 1, device=dev)[None, :]) % n
+    a0 = torch.minimum(idx[:, None].expand_as(near), near).reshape(-1)
+    b0 = torch.maximum(idx[:, None].expand_as(near), near).reshape(-1)
+    d = torch.cdist(C, C)
+    steps = (idx[:, None] - idx[None, :]).abs()
+    steps = torch.minimum(steps, n - steps)
+    d = torch.where(steps > far_steps, d, torch.full_like(d, float("inf")))
+    far = torch.topk(d, k_far, dim=1, largest=False).indices
+    a1 = torch.minimum(idx[:, None].expand_as(far), far).reshape(-1)
+    b1 = torch.maximum(idx[:, None].expand_as(far), far).reshape(-1)
+    key = torch.unique(torch.cat([a0 * n + b0, a1 * n + b1]))
+    return key // n, key % n
 
 
 def _trajectory(n: int, spacing: float, g, device):
@@ -362,19 +423,31 @@ def make_scene(name: str, seed: int = 0, device="cpu", **overrides) -> Scene:
         jj = ii + torch.arange(1, half + 1, device=device)[None, :]
         keep = jj < n
         cam_i, cam_j = ii[keep], jj[keep]
+    elif kind == "loop":
+        R, C = _cams_loop(n, cfg["laps"], g, device)
+        X = _ball_points(cfg["n_pts"], g, device)
+        cam_i, cam_j = _loop_pairs(C, cfg["path_nb"], cfg["knn"] - 2 * cfg["path_nb"],
+                                   n // (4 * cfg["laps"]))
     else:
         raise ValueError(kind)
 
     cam_i = cam_i.to(torch.int64)
     cam_j = cam_j.to(torch.int64)
     B = cam_i.shape[0]
+    want = None if kind == "ring" else _draw_counts(cfg["counts"], B, g, device)
     if kind == "trajectory":
         cand_lo, cand_hi = _trajectory_windows(s_cam, s_pt, cam_i, cam_j, cfg["depth"][1], f, W)
+    elif kind == "loop":
+        # every camera sees most of the cloud: a random window of about twice the wanted count
+        # of (unordered, hence random) points holds enough co-visible candidates
+        size = torch.clamp(2 * want + 64, max=X.shape[0])
+        u = torch.rand(B, dtype=F64, generator=g, device=device)
+        cand_lo = torch.floor(u * (X.shape[0] - size + 1).to(F64)).to(torch.int64)
+        cand_hi = cand_lo + size
     else:
         cand_lo = torch.zeros(B, dtype=torch.int64, device=device)
         cand_hi = torch.full((B,), X.shape[0], dtype=torch.int64, device=device)
 
-    want = None if kind == "ring" else _draw_counts(cfg["counts"], B, g, device)
     pid, pt = _covisible_matches(R, C, X, cam_i, cam_j, cand_lo, cand_hi, want,
                                  cfg.get("keep", 1.0), f, W, H, g, device)
     # drop pairs that received no matches and renumber (every pair must be non-empty)
@@ -466,15 +539,15 @@ def perturb_poses(R, t, cam_i, cam_j, rot_deg: float, trans_frac: float, g, kind
     centre moved by a random vector.
 
     The move is `trans_frac` of the camera's distance from the scene centre for object-centred
-    scenes (ring, sphere) and `trans_frac` of the median pair baseline for trajectories, where
-    the distance to the world origin has no meaning.
+    scenes (ring, sphere) and `trans_frac` of the median pair baseline for trajectories (open or
+    closed), whose cameras stand much closer to their neighbours than to the scene centre.
     """
     n = R.shape[0]
     device = R.device
     axis = _random_unit(n, g, device)
     R0 = rotation_exp(axis * math.radians(rot_deg)) @ R
     C = -torch.einsum("nba,nb->na", R, t)
-    if kind == "trajectory":
+    if kind in ("trajectory", "loop"):
         base = torch.median(torch.linalg.norm(C[cam_i] - C[cam_j], dim=-1))
         mag = trans_frac * base * torch.ones(n, 1, dtype=F64, device=device)
     else:

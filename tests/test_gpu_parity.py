@@ -1,9 +1,12 @@
 """Parity of the CUDA path (through the C ABI) against the FP64 oracle on identical inputs.
 
-Tolerances (derivation in the design notes):
-  * loss: relative 1e-4; gradient: max |g_gpu - g_oracle| <= 1e-4 * max |g_oracle| over the
-    whole (n_cams x 6) gradient (components near zero are dominated by cancellation, so an
-    element-wise relative bound would be meaningless there).
+Tolerances:
+  * loss: relative 1e-4 (FP32 per-point-pair terms summed per warp range and then in FP64).
+  * gradient: max |g_gpu - g_oracle| <= 1e-4 * max |g_oracle| over the whole (n_cams x 6)
+    gradient, and per camera and block (rotation, centre) |dg_k| <= 1e-4 |g_k| + 1e-7 max |g|
+    (tests/bounds.py states why: the FP32 pair sums carry about 1e-7 of their gross magnitude,
+    so a component that cancels to near zero cannot be held to a purely relative bound); for the
+    L1 objective plus the largest change of the sign decisions within the residual bound.
   * residuals: absolute 2e-6 in normalized units (FP32 forward error of a 3x3 bilinear form
     with |E| <= 1, |x| <= 1: about 12 roundings of terms <= 3, i.e. < 12 * 2^-24 * 3).
   * IRLS mask: identical except where the oracle's |eps| is within that residual bound of
@@ -19,6 +22,7 @@ import torch
 
 import oracle as O
 import scenegen
+from bounds import assert_grad_close, l1_flip_allowance
 import paper_2605_18052_gb300 as fm
 from paper_2605_18052_gb300 import build
 
@@ -48,9 +52,8 @@ def _oracle_inputs(sc, storage, delta=1e-6):
     return prob
 
 
-def _assert_grad_close(g, ref, tol=1e-4):
-    err = np.abs(g - ref).max()
-    assert err <= tol * np.abs(ref).max(), (err, np.abs(ref).max())
+def _assert_grad_close(g, ref, tol=1e-4, allowance=None):
+    assert_grad_close(g, ref, tol, allowance=allowance)
 
 
 def _gpu_problem(sc, R, t, **opt):
@@ -76,7 +79,8 @@ def test_loss_grad_parity(name, loss, storage):
         l_gpu, g_gpu = gp.loss_grad()
     l_or, g_or = O.loss_grad(prob, R0, c0, w, loss)
     assert l_gpu == pytest.approx(l_or, rel=1e-4)
-    _assert_grad_close(g_gpu, g_or)
+    allow = l1_flip_allowance(prob, R0, c0, O.residuals(prob, R0, c0), RESID_ATOL) if loss == "l1" else None
+    _assert_grad_close(g_gpu, g_or, allowance=allow)
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])

@@ -13,6 +13,7 @@ import torch
 
 import oracle as O
 import scenegen
+from bounds import assert_grad_close
 import paper_2605_18052_gb300 as fm
 from paper_2605_18052_gb300 import build
 
@@ -40,8 +41,7 @@ def _gpu_problem(sc, R, t, **opt):
 
 
 def _assert_grad_close(g, ref, tol=1e-4):
-    err = np.abs(g - ref).max()
-    assert err <= tol * np.abs(ref).max(), (err, np.abs(ref).max())
+    assert_grad_close(g, ref, tol)
 
 
 def _moved(R, c, seed, deg, frac):

@@ -1,6 +1,10 @@
-"""The seeded input generators deliver what the design notes state (no method arithmetic is
-involved): sizes, outlier fractions, match-score distributions and the relative-pose inputs of
-the global stages."""
+"""The seeded input generators keep their contract (no method arithmetic is involved): every
+scene has the outlier fraction its configuration names, every image pair has point pairs and
+every camera takes part in a pair; match scores follow Beta(4, 2) for inliers and Beta(2, 3) for
+outliers; initial poses are turned by exactly 5 degrees and moved by 10% of the stated distance;
+the closed trajectory closes on itself and links every lap to the others; and the relative
+rotations and translations handed to the global stages carry the stated noise and wrong-pair
+fraction."""
 import numpy as np
 import pytest
 
@@ -65,3 +69,30 @@ def test_relative_translations_noise_and_wrong_pairs():
     ang = np.degrees(np.arccos(np.clip((t * true).sum(1), -1, 1)))
     assert abs(out.mean() - 0.05) < 0.02
     assert ang[~out].max() < 5.0 and ang[out].mean() > 30.0
+
+
+def test_loop_scene_closes_and_links_laps():
+    # a reduced copy of the 1,000-camera closed trajectory (same layout and view graph, fewer
+    # points and matches so that it builds in seconds on the CPU)
+    sc = scenegen.make_scene("loop1000_o30", seed=0, n_pts=20_000, counts=("lognormal", 60.0, 0.9, 400))
+    n = sc.n_cams
+    R = sc.R_gt.numpy()
+    C = O.centres_from_poses(R, sc.t_gt.numpy())
+    ci, cj = sc.cam_i.numpy(), sc.cam_j.numpy()
+    assert n == 1000 and (ci < cj).all() and len(set(zip(ci, cj))) == len(ci)
+    assert abs(sc.outlier.numpy().mean() - 0.30) < 0.01
+    assert np.bincount(sc.pair_id.numpy(), minlength=sc.n_pairs).min() > 0
+    # the path closes: the last camera is as close to the first as neighbours are to each other
+    step = np.linalg.norm(np.diff(C, axis=0), axis=1)
+    assert np.linalg.norm(C[-1] - C[0]) < 2 * step.max()
+    # every camera looks at the point cloud: its optical axis passes within 1 of the origin
+    z = R[:, 2, :]                                    # viewing direction in world coordinates
+    miss = np.linalg.norm(np.cross(z, -C), axis=1)   # distance of the origin from the axis
+    assert (miss < 1.0).all()
+    # 8 neighbours along the path and 12 views of other laps for every camera
+    steps = np.abs(ci - cj)
+    steps = np.minimum(steps, n - steps)
+    far = steps > n // 20
+    deg_far = np.bincount(np.concatenate([ci[far], cj[far]]), minlength=n)
+    assert deg_far.min() >= 12 and far.mean() > 0.4
+    assert ((steps <= 4) | far).all()

@@ -1,7 +1,10 @@
 """Sharding across processes, tested without a GPU: the partition, and gloo ranks (world
 sizes 2 and 3) that each compute their shard with the oracle, all-reduce, and take the
 replicated optimiser step; the result must equal the single-process oracle on the whole
-problem."""
+problem. Both data planes of the sharded loop run: the host plane (gradient returned to the
+caller) and the device plane's control flow (gradient and loss written into one buffer that is
+all-reduced in place and read back by the optimiser step), here with CPU tensors and gloo in
+place of device memory and NCCL."""
 import os
 import socket
 
@@ -64,6 +67,21 @@ class _OracleShard:
         self.lr = (lr_rot, lr_c)
 
 
+class _OracleBufferShard(_OracleShard):
+    """The same oracle shard behind the device plane's interface (one buffer per iteration)."""
+
+    def new_buffer(self):
+        return torch.zeros(self.R.shape[0] * 6 + 1, dtype=torch.float64)
+
+    def loss_grad_into(self, buf):
+        loss, g = self.loss_grad()
+        buf[:-1] = torch.from_numpy(g.ravel())
+        buf[-1] = loss
+
+    def apply_gradient_from(self, buf):
+        self.apply_gradient(buf[:-1].numpy().reshape(-1, 6).copy())
+
+
 def _problem():
     import oracle as O
     import scenegen
@@ -74,7 +92,7 @@ def _problem():
     return prob, R0, c0
 
 
-def _rank(rank, world, port, out):
+def _rank(rank, world, port, out, plane="host"):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -84,8 +102,9 @@ def _rank(rank, world, port, out):
     b, e = partition_pairs(counts, world)[rank]
     lo, hi = shard_point_pairs(prob.pair_id, b, e)
     sub = O.Problem(prob.n_cams, prob.cam_i, prob.cam_j, prob.pair_id[lo:hi], prob.x1[lo:hi], prob.x2[lo:hi])
-    be = _OracleShard(sub, prob.n_pp, R0, c0)
+    be = (_OracleBufferShard if plane == "device" else _OracleShard)(sub, prob.n_pp, R0, c0)
     adj = ShardedAdjustment(be)
+    assert adj.device_plane == (plane == "device")
     # one sharded gradient vs the whole problem
     loss, g = be.loss_grad()
     buf = torch.from_numpy(np.concatenate([g.ravel(), [loss]]))
@@ -98,8 +117,8 @@ def _rank(rank, world, port, out):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_gloo_ranks_match_single_process(world):
+@pytest.mark.parametrize("world,plane", [(2, "host"), (3, "host"), (2, "device")])
+def test_gloo_ranks_match_single_process(world, plane):
     import oracle as O
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -107,7 +126,7 @@ def test_gloo_ranks_match_single_process(world):
     ctx = mp.get_context("spawn")
     manager = ctx.Manager()
     out = manager.dict()
-    mp.start_processes(_rank, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+    mp.start_processes(_rank, args=(world, port, out, plane), nprocs=world, join=True, start_method="spawn")
     prob, R0, c0 = _problem()
     l_full, g_full = O.loss_grad(prob, R0, c0, np.ones(prob.n_pp))
     for r in range(world):

@@ -2,11 +2,14 @@
 memory owned by another memory manager, or a loop that cannot afford cudaMalloc's implicit
 device synchronisation). Its intermediates live in a fixed __device__ array of the library.
 
-Checked through the C ABI against the existing entry point (fm_create_problem +
-fm_loss_grad) with the parity tolerance used for the oracle (loss relative 1e-4, gradient
-within 1e-4 of its largest entry), on two calls in a row of different sizes (stale scratch
-from the first call must not leak into the second), plus: a repeated call is bit-identical,
-device free memory does not change across a call, and sizes beyond the limits are refused.
+Checked through the C ABI against the FP64 oracle and against the existing entry point
+(fm_create_problem + fm_loss_grad) with the parity tolerance of the other tests (loss relative
+1e-4; gradient within 1e-4 of its largest entry and per camera, tests/bounds.py), on two calls
+in a row of different sizes (stale scratch from the first call must not leak into the second),
+plus: a repeated call is bit-identical, device free memory does not change across a call,
+sizes beyond the limits are refused, and invalid device data (offsets that do not rise, a pair
+of one camera with itself, a coordinate beyond 8, a negative weight) is refused with FM_EINVAL
+after which a valid call still gives the right result from the shared array.
 This file is collected after the other parity files (only the full-size checks follow), so a
 run that stops at the first failure has run them first.
 """
@@ -16,7 +19,9 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import scenegen
+from bounds import assert_grad_close
 import paper_2605_18052_gb300 as fm
 from paper_2605_18052_gb300 import binding, build
 
@@ -52,13 +57,25 @@ def _inputs(sc, mode, seed):
     return R, t, w, d
 
 
-def _call(lib, sc, d, mode):
+def _status(lib, sc, d, mode):
     P = lambda x: ctypes.c_void_p(x.data_ptr())
-    st = lib.fm_loss_grad_noalloc(sc.n_cams, P(d["R"]), P(d["c"]), sc.n_pairs, P(d["ci"]), P(d["cj"]),
-                                  P(d["off"]), sc.n_pp, P(d["kp"]), P(d["w"]), mode, P(d["loss"]),
-                                  P(d["grad"]), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return lib.fm_loss_grad_noalloc(sc.n_cams, P(d["R"]), P(d["c"]), sc.n_pairs, P(d["ci"]), P(d["cj"]),
+                                    P(d["off"]), sc.n_pp, P(d["kp"]), P(d["w"]), mode, P(d["loss"]),
+                                    P(d["grad"]), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def _call(lib, sc, d, mode):
+    st = _status(lib, sc, d, mode)
     assert st == 0, lib.fm_last_error().decode()
     return float(d["loss"].item()), d["grad"].cpu().numpy().reshape(-1, 6)
+
+
+def _oracle(sc, R, t, w, mode):
+    prob = O.Problem.from_scene(sc)
+    c = O.centres_from_poses(R, t)
+    if mode == fm.FM_LOSS_IRLS:
+        return O.loss_grad(prob, R, c, w.astype(np.float64), "irls")
+    return O.loss_grad(prob, R, c, None, "l1")
 
 
 def _reference(sc, R, t, w, mode):
@@ -71,7 +88,7 @@ def _reference(sc, R, t, w, mode):
 
 def _close(l, g, l_ref, g_ref):
     assert l == pytest.approx(l_ref, rel=1e-4)
-    assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
+    assert_grad_close(g, g_ref)
 
 
 def test_noalloc_matches_loss_grad_on_two_calls(lib):
@@ -91,6 +108,8 @@ def test_noalloc_matches_loss_grad_on_two_calls(lib):
     free_after = torch.cuda.mem_get_info()[0]
     _close(l1, g1, *ref1)
     _close(l2, g2, *ref2)
+    _close(l1, g1, *_oracle(big, R1, t1, w1, fm.FM_LOSS_IRLS))
+    _close(l2, g2, *_oracle(small, R2, t2, w2, fm.FM_LOSS_L1))
     assert free_after == free_before
 
     l3, g3 = _call(lib, small, d2, fm.FM_LOSS_L1)        # same inputs again: same bits
@@ -105,3 +124,35 @@ def test_noalloc_refuses_sizes_beyond_its_limits(lib):
         st = lib.fm_loss_grad_noalloc(n_cams, z, z, n_pairs, z, z, z, n_pp, z, None, 0, z, z, None)
         assert st == -1
         assert "fm_loss_grad_noalloc" in lib.fm_last_error().decode()
+
+
+def test_noalloc_refuses_invalid_device_data_then_recovers(lib):
+    # each case corrupts one device input (all reads stay inside the caller's buffers), is
+    # refused with FM_EINVAL, and the valid call that follows still matches the oracle
+    sc = scenegen.make_scene("ring16", seed=6)
+    R, t, w, d = _inputs(sc, fm.FM_LOSS_IRLS, 3)
+    ref = _oracle(sc, R, t, w, fm.FM_LOSS_IRLS)
+
+    def corrupt(key, index, value, col=None):
+        saved = d[key].clone()
+        if col is None:
+            d[key][index] = value
+        else:
+            d[key][index, col] = value
+        st = _status(lib, sc, d, fm.FM_LOSS_IRLS)
+        msg = lib.fm_last_error().decode()
+        d[key].copy_(saved)
+        return st, msg
+
+    cases = [("off", 3, int(d["off"][2].item()), None),          # offsets do not rise
+             ("cj", 5, int(d["ci"][5].item()), None),             # cam_i == cam_j
+             ("ci", 0, sc.n_cams, None),                          # camera index out of range
+             ("kp", 7, 9.0, 2),                                   # |coordinate| > 8
+             ("kp", 11, float("nan"), 0),                         # non-finite coordinate
+             ("w", 13, -1.0, None)]                               # negative weight
+    for key, index, value, col in cases:
+        st, msg = corrupt(key, index, value, col)
+        assert st == -1, (key, index, value, msg)
+        assert "fm_loss_grad_noalloc" in msg
+        l, g = _call(lib, sc, d, fm.FM_LOSS_IRLS)
+        _close(l, g, *ref)
