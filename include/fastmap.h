@@ -335,6 +335,13 @@ FM_API fm_status fm_collect_features(fm_problem *p, double tau, int32_t round, v
  * n_active counts point pairs with |eps^| <= tau_cap. Synchronises. */
 FM_API fm_status fm_learned_weights(fm_problem *p, const fm_mlp *net, double tau, double tau_cap,
                                     int32_t round, int64_t *n_active);
+/* One learned IRLS round: fm_learned_weights(net, tau, tau_cap, round) followed by
+ * fm_step(n_iters), with the learned reweighting (features, MLP, weights, history) fused into the
+ * first iteration's pass over the point pairs: the same arithmetic, bit for bit, and one read of
+ * the keypoints less. n_iters >= 1; IRLS objective only. Writes the number of point pairs with
+ * |eps^| <= tau_cap to *n_active if it is not NULL (then synchronises; otherwise only enqueues). */
+FM_API fm_status fm_step_learned(fm_problem *p, const fm_mlp *net, double tau, double tau_cap,
+                                 int32_t round, int32_t n_iters, int64_t *n_active);
 /* Forget the residual history (the next call uses the current residuals as history). */
 FM_API fm_status fm_reset_history(fm_problem *p);
 
@@ -342,12 +349,23 @@ FM_API fm_status fm_reset_history(fm_problem *p);
 FM_API fm_status fm_synchronize(fm_problem *p);
 
 /*
- * Kernel timing: when enabled, fm_step records CUDA events around every launch of the
- * loss+gradient streaming kernel (and replays no graph). fm_kernel_time returns the summed
- * event time in milliseconds and the number of timed launches since enabling, and resets
- * both. Synchronises.
+ * Kernel timing: when enabled, the library records CUDA events around every launch of each
+ * pass over the point pairs listed below (fm_step and fm_step_irls then replay no graph, and a
+ * timed pass is launched without overlap with its neighbours). fm_pass_time returns, for one
+ * pass, the summed event time in milliseconds and the number of timed launches since enabling
+ * (or since the last fm_pass_time of that pass), and resets both; fm_kernel_time is
+ * fm_pass_time(FM_PASS_STREAM_LOSS). Synchronises.
  */
+enum {
+    FM_PASS_STREAM_LOSS = 0,      /* loss + adjoint pass of an iteration (fm_step, fm_step_irls) */
+    FM_PASS_STREAM_REWEIGHT = 1,  /* the first pass of fm_step_irls (reweighting fused) */
+    FM_PASS_QUAD_ACCUMULATE = 2,  /* the form pass of fm_preaggregate / fm_irls_preaggregate */
+    FM_PASS_LEARNED_LOSS = 3,     /* the first pass of fm_step_learned (learned reweighting fused) */
+    FM_PASS_PAIR_STATS = 4,       /* the image-pair statistics pass of fm_step_learned */
+    FM_NUM_PASSES = 5
+};
 FM_API fm_status fm_enable_kernel_timing(fm_problem *p, int32_t enable);
+FM_API fm_status fm_pass_time(fm_problem *p, int32_t pass, double *ms, int64_t *launches);
 FM_API fm_status fm_kernel_time(fm_problem *p, double *ms, int64_t *launches);
 
 /* ---- global translation (Sec. "Global Translation") ----------------------------------------------

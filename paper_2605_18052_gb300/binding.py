@@ -15,16 +15,19 @@ LIB_PATH = os.path.join(HERE, "libfastmap.so")
 
 FM_STORE_FP32, FM_STORE_FP16 = 0, 1
 FM_LOSS_IRLS, FM_LOSS_L1 = 0, 1
+# timed passes (fm_pass_time)
+PASS_STREAM_LOSS, PASS_STREAM_REWEIGHT, PASS_QUAD_ACCUMULATE, PASS_LEARNED_LOSS, PASS_PAIR_STATS = range(5)
 
 EXPORTED = [
     "fm_default_options", "fm_create_problem", "fm_destroy_problem", "fm_problem_info",
     "fm_get_poses", "fm_set_poses", "fm_get_params", "fm_set_params", "fm_set_params_device", "fm_set_weights", "fm_get_weights", "fm_irls_weights",
     "fm_loss_grad", "fm_loss_grad_device", "fm_residuals", "fm_step", "fm_step_irls", "fm_last_loss",
     "fm_set_learning_rate", "fm_reset_optimizer", "fm_get_state", "fm_set_state",
-    "fm_synchronize", "fm_apply_gradient", "fm_enable_kernel_timing", "fm_kernel_time", "fm_loss_grad_noalloc",
+    "fm_synchronize", "fm_apply_gradient", "fm_enable_kernel_timing", "fm_kernel_time", "fm_pass_time",
+    "fm_loss_grad_noalloc",
     "fm_status_string", "fm_last_error", "fm_mlp_num_params", "fm_mlp_create", "fm_mlp_destroy",
     "fm_mlp_get_params", "fm_mlp_set_params", "fm_mlp_train_step", "fm_mlp_gradient", "fm_mlp_forward",
-    "fm_set_scores", "fm_collect_features", "fm_learned_weights", "fm_reset_history",
+    "fm_set_scores", "fm_collect_features", "fm_learned_weights", "fm_step_learned", "fm_reset_history",
     "fm_preaggregate", "fm_irls_preaggregate", "fm_loss_grad_quadratic", "fm_step_quadratic",
     "fm_set_focal_learning_rate", "fm_get_focal_scales", "fm_set_focal_scales", "fm_get_focal_gradient",
     "fm_translation_default_options", "fm_translation_create", "fm_translation_destroy",
@@ -96,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "fm_apply_gradient": (I32, [P, P, I32]),
         "fm_enable_kernel_timing": (I32, [P, I32]),
         "fm_kernel_time": (I32, [P, P, P]),
+        "fm_pass_time": (I32, [P, I32, P, P]),
         "fm_loss_grad_noalloc": (I32, [I32, P, P, I32, P, P, P, I64, P, P, I32, P, P, P]),
         "fm_mlp_num_params": (I32, []),
         "fm_mlp_create": (I32, [P, P]),
@@ -108,6 +112,7 @@ def load_library(path: str = LIB_PATH):
         "fm_set_scores": (I32, [P, P, I32]),
         "fm_collect_features": (I32, [P, D, I32, P]),
         "fm_learned_weights": (I32, [P, P, D, D, I32, P]),
+        "fm_step_learned": (I32, [P, P, D, D, I32, I32, P]),
         "fm_reset_history": (I32, [P]),
         "fm_preaggregate": (I32, [P]),
         "fm_irls_preaggregate": (I32, [P, D, P]),
@@ -301,6 +306,15 @@ class Problem:
                                                  int(round_index), ctypes.byref(n)))
         return n.value
 
+    def step_learned(self, net: "Mlp", tau: float, tau_cap: float, round_index: int, n_iters: int,
+                     count: bool = False):
+        """One learned IRLS round: the learned reweighting fused into the first of n_iters
+        iterations. Returns the number of point pairs with |eps| <= tau_cap if `count`."""
+        n = ctypes.c_int64()
+        _check(load_library().fm_step_learned(self._h, net._h, float(tau), float(tau_cap), int(round_index),
+                                              int(n_iters), ctypes.byref(n) if count else None))
+        return n.value if count else None
+
     def reset_history(self):
         _check(load_library().fm_reset_history(self._h))
 
@@ -432,6 +446,13 @@ class Problem:
         ms = ctypes.c_double()
         n = ctypes.c_int64()
         _check(load_library().fm_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def pass_time(self, which: int):
+        """(summed ms, launches) of one timed pass (PASS_*) since the last call; resets it."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(load_library().fm_pass_time(self._h, int(which), ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
 

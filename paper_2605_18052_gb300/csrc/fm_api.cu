@@ -51,8 +51,9 @@ struct fm_problem {
     bool quad_valid = false;              // d.quad holds the form of the current weights
     cudaGraphExec_t qgraph = nullptr, qgraph8 = nullptr;  // quadratic-path iterations
     cudaGraphExec_t rgraph = nullptr;     // one iteration whose pass is fused with the reweighting
-    std::vector<cudaEvent_t> tev;   // timing events, pairs (start, end)
-    size_t tev_used = 0;
+    // timing events per timed pass (fm_pass_time), pairs (start, end)
+    std::vector<cudaEvent_t> tev[FM_NUM_PASSES];
+    size_t tev_used[FM_NUM_PASSES] = {};
     int input_was_sorted = 0;
     int64_t device_bytes = 0;
     std::vector<void *> allocs;
@@ -156,32 +157,44 @@ fm_status check_options(const fm_options *o) {
     return FM_OK;
 }
 
-// one optimiser iteration (three launches, chained with programmatic dependent launch);
-// `first` = the iteration does not follow another one in this chain
-void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed, bool first, bool reweight = false) {
-    launch_pair_setup(p->d, s, true, !first);
-    if (reweight) {   // the round's reweighting fused into this pass (not part of kernel timing)
-        launch_stream_reweight(p->d, s, true);
-        launch_camera_step(p->d, true, s, true);
-        return;
-    }
-    if (timed && p->tev_used + 2 > p->tev.size()) {
+// CUDA events around a pass when kernel timing is on: time_begin returns whether the pass is
+// timed (then the caller launches it without programmatic serialisation and calls time_end)
+bool time_begin(fm_problem *p, int pass, cudaStream_t s) {
+    if (!p->timing) return false;
+    std::vector<cudaEvent_t> &ev = p->tev[pass];
+    if (p->tev_used[pass] + 2 > ev.size()) {
         for (int k = 0; k < 64; ++k) {
             cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) break;   // reported by the call's error check
-            p->tev.push_back(e);
+            if (cudaEventCreate(&e) != cudaSuccess) break;   // the pass then runs untimed
+            ev.push_back(e);
         }
     }
-    if (timed && p->tev_used + 2 <= p->tev.size()) {
-        cudaEventRecord(p->tev[p->tev_used], s);
-        launch_stream_loss(p->d, s, false);
-        cudaEventRecord(p->tev[p->tev_used + 1], s);
-        p->tev_used += 2;
+    if (p->tev_used[pass] + 2 > ev.size()) return false;
+    cudaEventRecord(ev[p->tev_used[pass]], s);
+    return true;
+}
+
+void time_end(fm_problem *p, int pass, cudaStream_t s) {
+    cudaEventRecord(p->tev[pass][p->tev_used[pass] + 1], s);
+    p->tev_used[pass] += 2;
+}
+
+// one optimiser iteration (three launches, chained with programmatic dependent launch);
+// `first` = the iteration does not follow another one in this chain; `reweight`: the round's
+// reweighting fused into this iteration's pass
+void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed, bool first, bool reweight = false) {
+    launch_pair_setup(p->d, s, true, !first);
+    const int pass = reweight ? FM_PASS_STREAM_REWEIGHT : FM_PASS_STREAM_LOSS;
+    if (timed && time_begin(p, pass, s)) {
+        if (reweight) launch_stream_reweight(p->d, s, false);
+        else launch_stream_loss(p->d, s, false);
+        time_end(p, pass, s);
         launch_camera_step(p->d, true, s, false);
-    } else {
-        launch_stream_loss(p->d, s, true);
-        launch_camera_step(p->d, true, s, true);
+        return;
     }
+    if (reweight) launch_stream_reweight(p->d, s, true);
+    else launch_stream_loss(p->d, s, true);
+    launch_camera_step(p->d, true, s, true);
 }
 
 // `iters` chained iterations and the closing finalize launch; `quad`: fused steps on the
@@ -231,7 +244,8 @@ void free_problem(fm_problem *p) {
     if (p->qgraph) cudaGraphExecDestroy(p->qgraph);
     if (p->qgraph8) cudaGraphExecDestroy(p->qgraph8);
     if (p->rgraph) cudaGraphExecDestroy(p->rgraph);
-    for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
+    for (auto &ev : p->tev)
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
     if (p->s) cudaStreamDestroy(p->s);
@@ -692,6 +706,45 @@ FM_API fm_status fm_learned_weights(fm_problem *p, const fm_mlp *net, double tau
     return FM_OK;
 }
 
+FM_API fm_status fm_step_learned(fm_problem *p, const fm_mlp *net, double tau, double tau_cap, int32_t round,
+                                 int32_t n_iters, int64_t *n_active) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!net) return fail(FM_EINVAL, "net must not be NULL");
+    if (!(tau > 0.0) || std::isinf(tau)) return fail(FM_EINVAL, "tau must be finite and > 0");
+    if (std::isnan(tau_cap) || tau_cap < 0.0) return fail(FM_EINVAL, "tau_cap must be >= 0 (may be +inf)");
+    if (round < 0) return fail(FM_EINVAL, "round must be >= 0");
+    if (n_iters < 1) return fail(FM_EINVAL, "n_iters must be >= 1");
+    if (p->d.loss != FM_LOSS_IRLS) return fail(FM_EINVAL, "the fused reweighting needs the IRLS objective");
+    const float *master = nullptr;
+    const __nv_bfloat16 *wbf = nullptr;
+    fm_internal_mlp_params(net, &master, &wbf);
+    FM_CUDA(join_in(p));
+    FM_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(unsigned long long), p->s));
+    launch_pair_setup(p->d, p->s);
+    const bool ts = time_begin(p, FM_PASS_PAIR_STATS, p->s);
+    launch_pair_stats(p->d, (float)tau, p->s);
+    if (ts) time_end(p, FM_PASS_PAIR_STATS, p->s);
+    const bool tl = time_begin(p, FM_PASS_LEARNED_LOSS, p->s);
+    launch_learned_loss(p->d, master, wbf, (float)tau, std::isinf(tau_cap) ? INFINITY : (float)tau_cap, round,
+                        p->hist_valid, p->s, false);
+    if (tl) time_end(p, FM_PASS_LEARNED_LOSS, p->s);
+    launch_camera_step(p->d, true, p->s, !tl);
+    launch_finalize(p->d, true, p->s, !tl);
+    FM_CUDA(cudaGetLastError());
+    p->quad_valid = false;
+    p->hist_valid = 1;
+    unsigned long long cnt = 0;
+    if (n_active) FM_CUDA(cudaMemcpyAsync(&cnt, p->d.counter, sizeof cnt, cudaMemcpyDeviceToHost, p->s));
+    if (n_iters > 1)
+        if (fm_status st = fm_step(p, n_iters - 1)) return st;
+    if (n_active) {
+        if (fm_status st = check_device_errors(p)) return st;
+        *n_active = (int64_t)cnt;
+    }
+    FM_CUDA(join_out(p));
+    return FM_OK;
+}
+
 FM_API fm_status fm_irls_weights(fm_problem *p, double tau, int64_t *n_active) {
     if (fm_status st = check_problem(p)) return st;
     if (std::isnan(tau) || tau < 0.0) return fail(FM_EINVAL, "tau must be >= 0 (may be +inf)");
@@ -793,8 +846,8 @@ FM_API fm_status fm_step_irls(fm_problem *p, double tau, int32_t n_iters, int64_
     FM_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(unsigned long long), p->s));
     p->quad_valid = false;
     if (p->timing || !p->opt.use_graph) {
-        enqueue_iteration(p, p->s, false, true, true);
-        launch_finalize(p->d, true, p->s, true);
+        enqueue_iteration(p, p->s, p->timing, true, true);
+        launch_finalize(p->d, true, p->s, !p->timing);
         FM_CUDA(cudaGetLastError());
     } else {
         if (!p->rgraph) {
@@ -975,7 +1028,10 @@ FM_API fm_status fm_preaggregate(fm_problem *p) {
     FM_CUDA(join_in(p));
     if (fm_status st = quad_prepare(p)) return st;
     launch_pair_setup(p->d, p->s);
+    const bool tq = time_begin(p, FM_PASS_QUAD_ACCUMULATE, p->s);
     launch_quad_accumulate(p->d, -1.f, p->s);
+    if (tq) time_end(p, FM_PASS_QUAD_ACCUMULATE, p->s);
+    launch_quad_combine(p->d, p->s);
     FM_CUDA(cudaGetLastError());
     p->quad_valid = true;
     FM_CUDA(join_out(p));
@@ -989,7 +1045,10 @@ FM_API fm_status fm_irls_preaggregate(fm_problem *p, double tau, int64_t *n_acti
     if (fm_status st = quad_prepare(p)) return st;
     FM_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(unsigned long long), p->s));
     launch_pair_setup(p->d, p->s);
+    const bool tq = time_begin(p, FM_PASS_QUAD_ACCUMULATE, p->s);
     launch_quad_accumulate(p->d, std::isinf(tau) ? INFINITY : (float)tau, p->s);
+    if (tq) time_end(p, FM_PASS_QUAD_ACCUMULATE, p->s);
+    launch_quad_combine(p->d, p->s);
     FM_CUDA(cudaGetLastError());
     p->quad_valid = true;
     unsigned long long cnt = 0;
@@ -1050,24 +1109,29 @@ FM_API fm_status fm_enable_kernel_timing(fm_problem *p, int32_t enable) {
     if (fm_status st = check_problem(p)) return st;
     FM_CUDA(cudaStreamSynchronize(p->s));
     p->timing = enable != 0;
-    p->tev_used = 0;
+    for (size_t &u : p->tev_used) u = 0;
+    return FM_OK;
+}
+
+FM_API fm_status fm_pass_time(fm_problem *p, int32_t pass, double *ms, int64_t *launches) {
+    if (fm_status st = check_problem(p)) return st;
+    if (!ms || !launches) return fail(FM_EINVAL, "ms and launches must not be NULL");
+    if (pass < 0 || pass >= FM_NUM_PASSES) return fail(FM_EINVAL, "unknown pass");
+    FM_CUDA(cudaStreamSynchronize(p->s));
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < p->tev_used[pass]; k += 2) {
+        float t = 0.f;
+        FM_CUDA(cudaEventElapsedTime(&t, p->tev[pass][k], p->tev[pass][k + 1]));
+        total += t;
+    }
+    *ms = total;
+    *launches = (int64_t)(p->tev_used[pass] / 2);
+    p->tev_used[pass] = 0;
     return FM_OK;
 }
 
 FM_API fm_status fm_kernel_time(fm_problem *p, double *ms, int64_t *launches) {
-    if (fm_status st = check_problem(p)) return st;
-    if (!ms || !launches) return fail(FM_EINVAL, "ms and launches must not be NULL");
-    FM_CUDA(cudaStreamSynchronize(p->s));
-    double total = 0.0;
-    for (size_t k = 0; k + 1 < p->tev_used; k += 2) {
-        float t = 0.f;
-        FM_CUDA(cudaEventElapsedTime(&t, p->tev[k], p->tev[k + 1]));
-        total += t;
-    }
-    *ms = total;
-    *launches = (int64_t)(p->tev_used / 2);
-    p->tev_used = 0;
-    return FM_OK;
+    return fm_pass_time(p, FM_PASS_STREAM_LOSS, ms, launches);
 }
 
 FM_API const char *fm_status_string(fm_status s) {

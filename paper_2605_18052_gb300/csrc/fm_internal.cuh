@@ -110,8 +110,10 @@ constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_H;               // 1
 constexpr int MLP_NPARAM = MLP_OFF_B3 + 1;                   // 1377
 constexpr float LOG_FLOOR = 1e-6f;
 
-// quadratic form: accumulate at the current poses and weights; per-iteration evaluation
+// quadratic form: accumulate at the current poses and weights (range partials), combine them
+// into per-pair records; per-iteration evaluation
 void launch_quad_accumulate(const DevProblem &d, float tau, cudaStream_t s);
+void launch_quad_combine(const DevProblem &d, cudaStream_t s);
 // one fused step on the form: iteration `it` of a chain (Adam step count *d.step + 1 + it),
 // camera records read from cam_src and written to cam_dst (apply = false: gradient and loss only)
 void launch_quad_step(const DevProblem &d, int it, const float *cam_src, float *cam_dst, bool apply,
@@ -124,6 +126,9 @@ void launch_learned_weights(const DevProblem &d, const float *mlp_master, const 
                             float tau, float tau_cap, int round, int hist_valid, cudaStream_t s);
 void launch_collect_features(const DevProblem &d, float tau, int round, int hist_valid,
                              __nv_bfloat16 *feat_input_order, cudaStream_t s);
+// the learned reweighting fused with the loss + adjoint pass (slots, weights, history, kept count)
+void launch_learned_loss(const DevProblem &d, const float *mlp_master, const __nv_bfloat16 *mlp_bf16, float tau,
+                         float tau_cap, int round, int hist_valid, cudaStream_t s, bool pdl);
 
 // ---- kernels launched by the API layer (fm_kernels.cu) ----------------------------------------
 void launch_cam_prep(const DevProblem &d, cudaStream_t s);

@@ -15,61 +15,6 @@
 
 namespace fm {
 
-// ---- loss + adjoint -----------------------------------------------------------------------------
-// acc[0..8] = sum s * o2 o1^T (row-major), acc[9] = sum of loss terms, with s = w*eps (IRLS,
-// the factor 2/Z is applied later) or sign(eps) (L1). Each finished (image pair, warp range)
-// intersection is reduced by a warp butterfly into its own slot n + r; no atomics, no fences,
-// a fixed summation order.
-template <int MODE>
-struct LossBody {
-    const DevProblem &d;
-    float acc[10];
-    __device__ explicit LossBody(const DevProblem &dd) : d(dd) {
-#pragma unroll
-        for (int i = 0; i < 10; ++i) acc[i] = 0.f;
-    }
-    __device__ __forceinline__ void point(int, float e, float x1, float y1, float x2, float y2,
-                                          float w) {
-        float s;
-        if (MODE == MODE_LOSS_IRLS) {
-            s = w * e;
-            acc[9] = fmaf(s, e, acc[9]);
-        } else {
-            s = e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f);
-            acc[9] += fabsf(e);
-        }
-        const float a = s * x2, b = s * y2;
-        acc[0] = fmaf(a, x1, acc[0]);
-        acc[1] = fmaf(a, y1, acc[1]);
-        acc[2] += a;
-        acc[3] = fmaf(b, x1, acc[3]);
-        acc[4] = fmaf(b, y1, acc[4]);
-        acc[5] += b;
-        acc[6] = fmaf(s, x1, acc[6]);
-        acc[7] = fmaf(s, y1, acc[7]);
-        acc[8] += s;
-    }
-    __device__ __forceinline__ void segment_begin(int) {}
-    __device__ __forceinline__ void segment_end(int seg, int r, int lane, bool) {
-#pragma unroll
-        for (int i = 0; i < 10; ++i) {
-            float v = acc[i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            acc[i] = v;
-        }
-        if (lane == 0) {
-            float4 *s = reinterpret_cast<float4 *>(d.slots + (size_t)(seg + r) * SLOT);
-            s[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-            s[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-            s[2] = make_float4(acc[8], acc[9], 0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < 10; ++i) acc[i] = 0.f;
-    }
-    __device__ __forceinline__ void group_done(int64_t, int64_t, int) {}
-};
-
 template <int STORE, int MODE>
 __global__ void __launch_bounds__(CTA_WARPS * 32, 4) k_stream_loss(DevProblem d) {
     pdl_wait();     // pair geometry of this pass

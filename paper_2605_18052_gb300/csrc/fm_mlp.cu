@@ -82,6 +82,14 @@ __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
     return *reinterpret_cast<const unsigned *>(&v);
 }
 
+// max(lo, 0) and max(hi, 0) rounded to BF16 and packed (lo in the low half): one instruction,
+// the same bits as pack_bf16(fmaxf(lo, 0), fmaxf(hi, 0))
+__device__ __forceinline__ unsigned pack_relu_bf16(float lo, float hi) {
+    unsigned d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
 // The per-lane B fragments and bias slices of the three layers.
 // For lane (g = lane / 4, t = lane % 4): B fragment of an n-tile j holds W[k][8j + g] for
 // k = 2t, 2t+1 (b0) and k = 2t+8, 2t+9 (b1); accumulator columns are 8j + 2t, 8j + 2t + 1.
@@ -141,10 +149,10 @@ __device__ __forceinline__ void mlp_tiles(const MlpFrag &f, const __nv_bfloat16 
         unsigned a2[2][4];
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
-            a2[kk][0] = pack_bf16(fmaxf(h1[2 * kk][0], 0.f), fmaxf(h1[2 * kk][1], 0.f));
-            a2[kk][1] = pack_bf16(fmaxf(h1[2 * kk][2], 0.f), fmaxf(h1[2 * kk][3], 0.f));
-            a2[kk][2] = pack_bf16(fmaxf(h1[2 * kk + 1][0], 0.f), fmaxf(h1[2 * kk + 1][1], 0.f));
-            a2[kk][3] = pack_bf16(fmaxf(h1[2 * kk + 1][2], 0.f), fmaxf(h1[2 * kk + 1][3], 0.f));
+            a2[kk][0] = pack_relu_bf16(h1[2 * kk][0], h1[2 * kk][1]);
+            a2[kk][1] = pack_relu_bf16(h1[2 * kk][2], h1[2 * kk][3]);
+            a2[kk][2] = pack_relu_bf16(h1[2 * kk + 1][0], h1[2 * kk + 1][1]);
+            a2[kk][3] = pack_relu_bf16(h1[2 * kk + 1][2], h1[2 * kk + 1][3]);
         }
         float h2[4][4];
 #pragma unroll
@@ -159,10 +167,10 @@ __device__ __forceinline__ void mlp_tiles(const MlpFrag &f, const __nv_bfloat16 
         unsigned a3[2][4];
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
-            a3[kk][0] = pack_bf16(fmaxf(h2[2 * kk][0], 0.f), fmaxf(h2[2 * kk][1], 0.f));
-            a3[kk][1] = pack_bf16(fmaxf(h2[2 * kk][2], 0.f), fmaxf(h2[2 * kk][3], 0.f));
-            a3[kk][2] = pack_bf16(fmaxf(h2[2 * kk + 1][0], 0.f), fmaxf(h2[2 * kk + 1][1], 0.f));
-            a3[kk][3] = pack_bf16(fmaxf(h2[2 * kk + 1][2], 0.f), fmaxf(h2[2 * kk + 1][3], 0.f));
+            a3[kk][0] = pack_relu_bf16(h2[2 * kk][0], h2[2 * kk][1]);
+            a3[kk][1] = pack_relu_bf16(h2[2 * kk][2], h2[2 * kk][3]);
+            a3[kk][2] = pack_relu_bf16(h2[2 * kk + 1][0], h2[2 * kk + 1][1]);
+            a3[kk][3] = pack_relu_bf16(h2[2 * kk + 1][2], h2[2 * kk + 1][3]);
         }
         float z[4] = {t == 0 ? f.b3 : 0.f, 0.f, t == 0 ? f.b3 : 0.f, 0.f};
         mma_bf16(z, a3[0], f.w3[0][0], f.w3[0][1]);
@@ -172,6 +180,12 @@ __device__ __forceinline__ void mlp_tiles(const MlpFrag &f, const __nv_bfloat16 
             ps[r1] = __frcp_rn(1.f + __expf(-z[2]));
         }
     }
+}
+
+// learned IRLS weight p / max(|eps|, delta) (fast quotient, within 2 ulp; every learned kernel
+// uses this one expression, so the fused and separate passes agree bit for bit)
+__device__ __forceinline__ float learned_weight(float p, float ae, float delta) {
+    return __fdividef(p, fmaxf(ae, delta));
 }
 
 // ---- features of a point pair ---------------------------------------------------------------------
@@ -188,7 +202,7 @@ struct LearnedBody {
     float st_mean, st_frac, st_cnt;
     float ae[PPL], le[PPL], sm[PPL], sf[PPL], sc[PPL];
     unsigned kept;
-    const MlpFrag *frag;
+    MlpFrag frag;     // the network's B fragments, in registers
     __nv_bfloat16 (*xs)[MLP_IN];
     float *ps;
     __nv_bfloat16 *feat_out;
@@ -240,13 +254,13 @@ struct LearnedBody {
         }
         if (!COLLECT) {
             __syncwarp();
-            mlp_tiles(*frag, xs, ps, GROUP / 16, lane);
+            mlp_tiles(frag, xs, ps, GROUP / 16, lane);
             __syncwarp();
             float w[PPL];
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
                 const bool in = q + k < p_end && ae[k] <= tau_cap;
-                w[k] = in ? ps[lane * PPL + k] / fmaxf(ae[k], delta) : 0.f;
+                w[k] = in ? learned_weight(ps[lane * PPL + k], ae[k], delta) : 0.f;
                 kept += in ? 1u : 0u;
             }
             if (STORE == FM_STORE_FP32) {
@@ -271,27 +285,25 @@ k_learned(DevProblem d, const float *master, const __nv_bfloat16 *wbf, float tau
     constexpr int GROUP = 32 * Fmt<STORE>::PPL;
     __shared__ __align__(16) __nv_bfloat16 xs[CTA_WARPS][GROUP][MLP_IN];
     __shared__ float ps[CTA_WARPS][GROUP];
-    __shared__ MlpFrag sfrag[32];   // per-lane fragments, shared by the CTA's warps
     __shared__ unsigned cta_kept;
     if (threadIdx.x == 0) cta_kept = 0;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (!COLLECT && w == 0) load_frag(sfrag[lane], master, wbf, lane);
     __syncthreads();
     const int r = blockIdx.x * CTA_WARPS + w;
-    const MlpFrag &frag = sfrag[lane];
     if (r < d.n_ranges) {
         LearnedBody<STORE, COLLECT> body(d);
+        if (!COLLECT) load_frag(body.frag, master, wbf, lane);
         body.log_tau = __logf(tau);
         body.tau_cap = tau_cap;
         body.delta = (float)d.delta;
         body.wscale = d.w_scale;
         body.round_f = round * 0.1f;
         body.hist_valid = hist_valid;
-        body.frag = &frag;
         body.xs = xs[w];
         body.ps = ps[w];
         body.feat_out = feat_out;
-        walk_range<STORE, false>(d, r, lane, body);
+        // one group in flight: the fragments take the registers a deeper unroll would use
+        walk_range<STORE, false, LearnedBody<STORE, COLLECT>, 1>(d, r, lane, body);
         unsigned k = body.kept;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
@@ -301,7 +313,172 @@ k_learned(DevProblem d, const float *master, const __nv_bfloat16 *wbf, float tau
     if (!COLLECT && threadIdx.x == 0 && cta_kept) atomicAdd(d.counter, (unsigned long long)cta_kept);
 }
 
+// ---- the learned reweighting fused with the round's first loss + adjoint pass -------------------
+// Same arithmetic as k_learned followed by k_stream_loss, one read of the keypoints instead of
+// two. Every group of 32 * PPL point pairs is handled in two phases:
+//   A: residual, features (with the statistics of each point pair's own image pair), the MLP on
+//      the group's rows (tensor cores, mma.sync), the weight (written, FP16-quantised for FP16
+//      storage), the residual history;
+//   B: the loss and adjoint sums of the group with those weights, closing every image pair that
+//      ended inside the group (warp butterfly into its slot n + r, as the streaming pass does).
+// Phase A walks the group's image pairs forward; phase B revisits the same image pairs from the
+// group's first one. The network's B fragments stay in registers for the whole kernel (reading
+// them from shared memory for every 16-row tile would move about 330 B of shared memory per
+// point pair); to make room, the keypoints stay packed between the phases and the current image
+// pair's E'_n and statistics are reloaded (from L1) at the start of every group.
+template <int STORE>
+__global__ void __launch_bounds__(CTA_WARPS * 32, 2)
+k_learned_loss(DevProblem d, const float *master, const __nv_bfloat16 *wbf, float tau, float tau_cap, int round,
+               int hist_valid) {
+    using F = Fmt<STORE>;
+    constexpr int PPL = F::PPL;
+    constexpr int GROUP = 32 * PPL;
+    __shared__ __align__(16) __nv_bfloat16 xs[CTA_WARPS][GROUP][MLP_IN];
+    __shared__ float ps[CTA_WARPS][GROUP];
+    __shared__ unsigned cta_kept;
+    if (threadIdx.x == 0) cta_kept = 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    MlpFrag frag;
+    load_frag(frag, master, wbf, lane);
+    pdl_wait();     // pair geometry and statistics of this pass
+    pdl_trigger();
+    __syncthreads();
+    const int r = blockIdx.x * CTA_WARPS + wid;
+    unsigned kept = 0;
+    if (r < d.n_ranges) {
+        const float log_tau = __logf(tau), delta = (float)d.delta, wscale = d.w_scale, round_f = round * 0.1f;
+        const int64_t p_begin = (int64_t)r * WR;
+        const int64_t p_end = min(p_begin + (int64_t)WR, d.n_pp);
+        int seg = d.range_pair[r];
+        int64_t seg_end = d.pair_off[seg + 1];
+        LossBody<MODE_LOSS_IRLS> loss(d);
+        const uint64_t pol = evict_first_policy();
+        for (int64_t gb = p_begin; gb < p_end; gb += GROUP) {
+            const int64_t q0 = gb + lane * PPL;
+            const typename F::Raw raw = F::load(d, q0, false, pol);
+            // score and history of the lane's point pairs (PPL consecutive halves)
+            float sco[PPL], lp[PPL];
+            if (PPL == 2) {
+                const float2 sv = __half22float2(reinterpret_cast<const __half2 *>(d.score)[q0 >> 1]);
+                const float2 hv = __half22float2(reinterpret_cast<const __half2 *>(d.le_hist)[q0 >> 1]);
+                sco[0] = sv.x;
+                sco[PPL - 1] = sv.y;
+                lp[0] = hv.x;
+                lp[PPL - 1] = hv.y;
+            } else {
+                sco[0] = __half2float(d.score[q0]);
+                lp[0] = __half2float(d.le_hist[q0]);
+            }
+            float e[PPL], le[PPL];
+#pragma unroll
+            for (int k = 0; k < PPL; ++k) e[k] = le[k] = 0.f;
+            // phase A
+            const int seg0 = seg;
+            const int64_t seg0_end = seg_end;
+            const int64_t g_end = min(gb + GROUP, p_end);
+            float E[9];
+            load_E(d.geo, seg, E);
+            float4 st = reinterpret_cast<const float4 *>(d.pstat)[seg];
+            int64_t lo = gb;
+            while (true) {
+                const int64_t hi = min(seg_end, p_end);
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) {
+                    const int64_t q = q0 + k;
+                    if (q >= lo && q < hi) {
+                        float x1, y1, x2, y2, unused;
+                        F::get(raw, k, x1, y1, x2, y2, unused);
+                        e[k] = epi(E, x1, y1, x2, y2);
+                        le[k] = __logf(fabsf(e[k]) + LOG_FLOOR);
+                        const float lpk = hist_valid ? lp[k] : le[k];
+                        float f[MLP_IN];
+                        f[0] = le[k] - log_tau;
+                        f[1] = le[k] - st.x;
+                        f[2] = lpk - le[k];
+                        f[3] = sco[k];
+                        f[4] = st.y;
+                        f[5] = st.z;
+                        f[6] = round_f;
+                        f[7] = lpk - log_tau;
+                        __align__(16) __nv_bfloat16 fb[MLP_IN];
+#pragma unroll
+                        for (int i = 0; i < MLP_IN; ++i) fb[i] = __float2bfloat16_rn(f[i]);
+                        *reinterpret_cast<uint4 *>(xs[wid][lane * PPL + k]) = *reinterpret_cast<const uint4 *>(fb);
+                    }
+                }
+                if (seg_end >= g_end) break;
+                lo = seg_end;
+                ++seg;
+                seg_end = d.pair_off[seg + 1];
+                load_E(d.geo, seg, E);
+                st = reinterpret_cast<const float4 *>(d.pstat)[seg];
+            }
+#pragma unroll
+            for (int k = 0; k < PPL; ++k)   // rows past the end of the range: any finite input
+                if (q0 + k >= p_end) *reinterpret_cast<uint4 *>(xs[wid][lane * PPL + k]) = make_uint4(0u, 0u, 0u, 0u);
+            __syncwarp();
+            mlp_tiles(frag, xs[wid], ps[wid], GROUP / 16, lane);
+            __syncwarp();
+            float w[PPL];
+#pragma unroll
+            for (int k = 0; k < PPL; ++k) {
+                const float ae = fabsf(e[k]);
+                const bool in = q0 + k < p_end && ae <= tau_cap;
+                const float wf = in ? learned_weight(ps[wid][lane * PPL + k], ae, delta) : 0.f;
+                w[k] = STORE == FM_STORE_FP32 ? wf : __half2float(__float2half_rn(wf * wscale));
+                kept += in ? 1u : 0u;
+            }
+            if (STORE == FM_STORE_FP32) {
+                static_cast<float *>(d.w)[q0] = w[0];
+                if (q0 < p_end) d.le_hist[q0] = __float2half_rn(le[0]);
+            } else {
+                reinterpret_cast<__half2 *>(d.w)[q0 >> 1] = __floats2half2_rn(w[0], w[PPL - 1]);
+                const __half2 hv = __floats2half2_rn(le[0], le[PPL - 1]);
+                if (q0 + 1 < p_end) reinterpret_cast<__half2 *>(d.le_hist)[q0 >> 1] = hv;
+                else if (q0 < p_end) d.le_hist[q0] = __low2half(hv);
+            }
+            __syncwarp();
+            // phase B
+            int sb = seg0;
+            int64_t sb_end = seg0_end;
+            lo = gb;
+            while (true) {
+                const int64_t hi = min(sb_end, p_end);
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) {
+                    const int64_t q = q0 + k;
+                    if (q >= lo && q < hi) {
+                        float x1, y1, x2, y2, unused;
+                        F::get(raw, k, x1, y1, x2, y2, unused);
+                        loss.point(k, e[k], x1, y1, x2, y2, w[k]);
+                    }
+                }
+                if (sb == seg) break;
+                loss.segment_end(sb, r, lane, false);
+                lo = sb_end;
+                ++sb;
+                sb_end = d.pair_off[sb + 1];
+            }
+        }
+        loss.segment_end(seg, r, lane, true);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    if (lane == 0 && kept) atomicAdd(&cta_kept, kept);
+    __syncthreads();
+    if (threadIdx.x == 0 && cta_kept) atomicAdd(d.counter, (unsigned long long)cta_kept);
+}
+
 static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+void launch_learned_loss(const DevProblem &d, const float *master, const __nv_bfloat16 *wbf, float tau,
+                         float tau_cap, int round, int hist_valid, cudaStream_t s, bool pdl) {
+    const dim3 grid(blocks_for(d.n_ranges, CTA_WARPS)), block(CTA_WARPS * 32);
+    if (d.storage == FM_STORE_FP32)
+        launch_k(k_learned_loss<FM_STORE_FP32>, grid, block, s, pdl, d, master, wbf, tau, tau_cap, round, hist_valid);
+    else
+        launch_k(k_learned_loss<FM_STORE_FP16>, grid, block, s, pdl, d, master, wbf, tau, tau_cap, round, hist_valid);
+}
 
 void launch_pair_stats(const DevProblem &d, float tau, cudaStream_t s) {
     const int grid = blocks_for(d.n_ranges, CTA_WARPS);

@@ -299,6 +299,9 @@ void launch_quad_accumulate(const DevProblem &d, float tau, cudaStream_t s) {
         if (d.storage == FM_STORE_FP32) k_quad_accumulate<FM_STORE_FP32, true><<<grid, block, 0, s>>>(d, tau);
         else k_quad_accumulate<FM_STORE_FP16, true><<<grid, block, 0, s>>>(d, tau);
     }
+}
+
+void launch_quad_combine(const DevProblem &d, cudaStream_t s) {
     k_quad_combine<<<blocks_for(d.n_pairs, 8), 256, 0, s>>>(d);
 }
 

@@ -391,66 +391,75 @@ __global__ void __launch_bounds__(RT_THREADS) k_rot_pair(DevRot t) {
     }
 }
 
-// warp per camera: gather d L/d R_k from its pairs (scaled 1/|P|), map through the 6D
-// representation, then Adam on the 6D parameters (apply) or write the gradient into pgrad's
-// camera view (apply = 0: t.q holds n_cams x 6 gradients); block partials of the loss
+// warp per camera: gather d L/d R_k from its pairs (scaled 1/|P|); then lanes 0..RT_CAMS-1 of
+// warp 0 map the block's cameras through the 6D representation and take the Adam step (apply)
+// or write the gradient (apply = 0: grad_out holds n_cams x 6 gradients), one camera per lane:
+// GB300's FP64 pipe charges a whole warp instruction per operation, so the FP64 tail runs once
+// per block instead of once per camera. Block partials of the loss.
 __global__ void __launch_bounds__(RT_CAMS * 32) k_rot_cam(DevRot t, int it, int apply, double *grad_out) {
-    __shared__ double s_blk[RT_CAMS];
+    __shared__ double s_g[RT_CAMS][10];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = blockIdx.x * RT_CAMS + warp;
     pdl_wait();     // pair gradients of this step
     pdl_trigger();
-    double lsum = 0.0;
-    if (k < t.n_cams) {
+    {
         double g[10];
 #pragma unroll
         for (int q = 0; q < 10; ++q) g[q] = 0.0;
-        for (int e = t.cam_off[k] + lane; e < t.cam_off[k + 1]; e += 32) {
-            const int ent = t.cam_ent[e];
-            const int n = ent >> 1, role = ent & 1;
-            const double *pg = t.pgrad + (size_t)n * 18 + (role ? 9 : 0);
+        if (k < t.n_cams) {
+            for (int e = t.cam_off[k] + lane; e < t.cam_off[k + 1]; e += 32) {
+                const int ent = t.cam_ent[e];
+                const int n = ent >> 1, role = ent & 1;
+                const double *pg = t.pgrad + (size_t)n * 18 + (role ? 9 : 0);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) g[q] += pg[q];
-            if (role == 0) g[9] += t.pdist[n];     // each pair's distance counted once
+                for (int q = 0; q < 9; ++q) g[q] += pg[q];
+                if (role == 0) g[9] += t.pdist[n];     // each pair's distance counted once
+            }
+            warp_sum<10>(g);
         }
-        warp_sum<10>(g);
-        lsum = g[9];
         if (lane == 0) {
-            const double inv_b = 1.0 / (double)t.n_pairs;
 #pragma unroll
-            for (int q = 0; q < 9; ++q) g[q] *= inv_b;
-            double ga[6];
-            rot_6d_backward(t.a + (size_t)k * 6, g, ga);
-            if (!apply) {
+            for (int q = 0; q < 10; ++q) s_g[warp][q] = g[q];
+        }
+    }
+    __syncthreads();
+    if (warp != 0 || lane >= RT_CAMS) return;
+    const int kc = blockIdx.x * RT_CAMS + lane;
+    if (kc < t.n_cams) {
+        const double inv_b = 1.0 / (double)t.n_pairs;
+        double g[9];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) grad_out[(size_t)k * 6 + q] = ga[q];
-            } else {
-                const long long ts = *t.step + 1 + it;
-                const float lr = (float)t.hyper[0], b1 = (float)t.hyper[1], b2 = (float)t.hyper[2],
-                            eps = (float)t.hyper[3];
-                const float bc1 = 1.f - powf(b1, (float)ts), bc2 = 1.f - powf(b2, (float)ts);
-                double *ak = t.a + (size_t)k * 6;
+        for (int q = 0; q < 9; ++q) g[q] = s_g[lane][q] * inv_b;
+        double ga[6];
+        rot_6d_backward(t.a + (size_t)kc * 6, g, ga);
+        if (!apply) {
 #pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const size_t o = (size_t)k * 6 + q;
-                    const float gq = (float)ga[q];
-                    const float mo = b1 * t.m[o] + (1.f - b1) * gq;
-                    const float vo = b2 * t.v[o] + (1.f - b2) * gq * gq;
-                    t.m[o] = mo;
-                    t.v[o] = vo;
-                    ak[q] -= (double)(lr * (mo / bc1) / (sqrtf(vo / bc2) + eps));
-                }
+            for (int q = 0; q < 6; ++q) grad_out[(size_t)kc * 6 + q] = ga[q];
+        } else {
+            const long long ts = *t.step + 1 + it;
+            const float lr = (float)t.hyper[0], b1 = (float)t.hyper[1], b2 = (float)t.hyper[2],
+                        eps = (float)t.hyper[3];
+            const float bc1 = 1.f - powf(b1, (float)ts), bc2 = 1.f - powf(b2, (float)ts);
+            double *ak = t.a + (size_t)kc * 6;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const size_t o = (size_t)kc * 6 + q;
+                const float gq = (float)ga[q];
+                const float mo = b1 * t.m[o] + (1.f - b1) * gq;
+                const float vo = b2 * t.v[o] + (1.f - b2) * gq * gq;
+                t.m[o] = mo;
+                t.v[o] = vo;
+                ak[q] -= (double)(lr * (mo / bc1) / (sqrtf(vo / bc2) + eps));
             }
         }
     }
-    if (lane == 0) s_blk[warp] = lsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if (lane == 0) {   // loss partial of the block, cameras in order
         double b = 0.0;
-        for (int w = 0; w < RT_CAMS; ++w) b += s_blk[w];
+        for (int w = 0; w < RT_CAMS; ++w) b += s_g[w][9];
         t.blk[blockIdx.x] = b;
     }
 }
+
 
 // rotations of the updated parameters (after a step) + loss of the step's evaluation
 __global__ void __launch_bounds__(RT_THREADS) k_rot_finish(DevRot t, int count) {

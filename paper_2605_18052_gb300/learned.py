@@ -73,14 +73,14 @@ def refine_learned(problem, net: Mlp, schedule: Schedule, callback=None, first_r
         problem.reset_history()
     for r in range(first_round, schedule.rounds):
         tau = schedule.tau(r)
-        problem.learned_weights(net, tau, tau, r)
         s = schedule.decay ** r
         problem.set_learning_rate(schedule.lr_rot * s, schedule.lr_c * s)
         if quadratic:
+            problem.learned_weights(net, tau, tau, r)
             problem.preaggregate()
             problem.step_quadratic(schedule.iters_per_round)
-        else:
-            problem.step(schedule.iters_per_round)
+        else:   # the reweighting fused into the round's first pass (fm_step_learned)
+            problem.step_learned(net, tau, tau, r, schedule.iters_per_round)
         if callback is not None:
             callback(r, problem)
     return problem
@@ -136,15 +136,16 @@ def train_from_scenes(config: str, seeds, rounds: int, collect_rounds: int, per_
 
 
 def time_to_accuracy(sc, arm: str, net: Mlp | None = None, storage: str = "fp16", max_rounds: int = 80,
-                     threshold_deg: float = 0.1, thresholds=(2.0, 1.0, 0.5, 0.25, 0.1)):
+                     threshold_deg: float = 0.1, thresholds=(2.0, 1.0, 0.5, 0.25, 0.1), schedule=None):
     """Device time of the refinement loop until the mean rotation error (after global
     alignment) is <= threshold_deg, and the time at which each of `thresholds` was first
     reached. The error is checked after every round and the check is not timed.
     arm: "irls" (plain reweighting) or "learned", each optionally with the suffix "_quad"
-    (iterations on the pre-aggregated quadratic form). Returns a dict."""
+    (iterations on the pre-aggregated quadratic form). `schedule` replaces the default schedule
+    (its rounds are ignored in favour of max_rounds). Returns a dict."""
     from . import metrics
     from .binding import Problem
-    sch = default_schedule(sc, max_rounds)
+    sch = default_schedule(sc, max_rounds) if schedule is None else schedule
     Rg = sc.R_gt.cpu().numpy()
     stream = torch.cuda.current_stream()
     total_ms, hist, first = 0.0, [], {}
@@ -166,8 +167,7 @@ def time_to_accuracy(sc, arm: str, net: Mlp | None = None, storage: str = "fp16"
                 gp.irls_preaggregate(tau)
                 gp.step_quadratic(sch.iters_per_round)
             elif arm == "learned":
-                gp.learned_weights(net, tau, tau, r)
-                gp.step(sch.iters_per_round)
+                gp.step_learned(net, tau, tau, r, sch.iters_per_round)
             elif arm == "learned_quad":
                 gp.learned_weights(net, tau, tau, r)
                 gp.preaggregate()

@@ -30,7 +30,7 @@ import math
 
 import torch
 
-__all__ = ["Scene", "CONFIGS", "make_scene", "perturb_poses", "rotation_exp"]
+__all__ = ["Scene", "CONFIGS", "make_scene", "perturb_poses", "rotation_exp", "fundamental_matrices"]
 
 F64 = torch.float64
 
@@ -88,13 +88,14 @@ class Scene:
 #               evaluated on seeds outside the training seeds 1000-1199).
 #   traj4000  : 4,000 cameras, 2M points, 25 neighbours (~5e4 pairs), Pareto(1.5) counts
 #               capped at 50k (~1.5e8 point pairs), 25% outliers, 1.5 px.
-#   loop1000  : 1,000 cameras along a random smooth closed trajectory that circles a 500k-point
-#               cloud in 5 laps at changing heights (every lap closes a loop and neighbouring
-#               laps revisit the same views), looking inward; 20 neighbours per camera: 8 along
-#               the path and 12 nearest views elsewhere on it (~1e4 pairs), log-normal counts
-#               (~5e7 point pairs), 20% outliers, 1 px.
+#   loop1000  : 1,000 cameras along a random smooth closed trajectory that winds 20 times
+#               around a 500k-point cloud while its height sweeps +-70 degrees of elevation and
+#               back (every lap closes a loop, neighbouring laps revisit the same views),
+#               looking inward; 20 neighbours per camera: 8 along the path and 12 nearest views
+#               of other laps (~1.2e4 pairs), log-normal counts (~6e7 point pairs), 20% outliers,
+#               1 px.
 #   loop1000_o30 : loop1000 with 30% outliers (learned-weight evaluation scene).
-#   loop4000  : loop1000's layout at the size of traj4000 (4,000 cameras, 2M points,
+#   loop4000  : the same layout at the size of traj4000 (4,000 cameras in 40 laps, 2M points,
 #               25 neighbours, Pareto(1.5) counts capped at 50k, 25% outliers, 1.5 px).
 CONFIGS = {
     "ring16": dict(kind="ring", n_cams=16, n_pts=2000, sigma_px=0.5, outlier=0.10,
@@ -113,11 +114,13 @@ CONFIGS = {
                      outlier=0.25, knn=25, counts=("pareto", 1.5, 1100.0, 50_000),
                      spacing=0.1, depth=(4.0, 16.0), iters=300),
     "loop1000": dict(kind="loop", n_cams=1000, n_pts=500_000, sigma_px=1.0, outlier=0.20,
-                     knn=20, path_nb=4, laps=5, counts=("lognormal", 3900.0, 0.9, 20_000), iters=300),
+                     knn=20, path_nb=4, laps=20, elev_deg=70.0, counts=("lognormal", 3900.0, 0.9, 20_000),
+                     iters=300),
     "loop1000_o30": dict(kind="loop", n_cams=1000, n_pts=500_000, sigma_px=1.0, outlier=0.30,
-                         knn=20, path_nb=4, laps=5, counts=("lognormal", 3900.0, 0.9, 20_000), iters=300),
+                         knn=20, path_nb=4, laps=20, elev_deg=70.0, counts=("lognormal", 3900.0, 0.9, 20_000),
+                         iters=300),
     "loop4000": dict(kind="loop", n_cams=4000, n_pts=2_000_000, sigma_px=1.5, outlier=0.25,
-                     knn=25, path_nb=5, laps=10, counts=("pareto", 1.5, 1100.0, 50_000), iters=300),
+                     knn=25, path_nb=5, laps=40, elev_deg=70.0, counts=("pareto", 1.5, 1100.0, 50_000), iters=300),
 }
 
 
@@ -231,7 +234,8 @@ def _cams_sphere(n: int, g, device, radius: float, jitter_deg: float):
     return rotation_exp(jit) @ R, C
 
 
-def _cams_loop(n: int, laps: int, g, device, radius: float = 3.0, jitter_deg: float = 10.0):
+def _cams_loop(n: int, laps: int, g, device, radius: float = 3.0, jitter_deg: float = 10.0,
+               elev_deg: float = 35.0):
     """Cameras along a random smooth closed trajectory around the origin, looking inward.
 
     The path winds `laps` times around the vertical axis; its elevation follows one slow
@@ -242,7 +246,7 @@ def _cams_loop(n: int, laps: int, g, device, radius: float = 3.0, jitter_deg: fl
     s = (torch.arange(n, dtype=F64, device=device) + 0.5) / n          # path parameter in [0, 1)
     theta = 2 * math.pi * laps * s
     phase = 2 * math.pi * float(torch.rand(1, dtype=F64, generator=g, device=device))
-    elev = math.radians(35.0) * torch.cos(2 * math.pi * s + phase)
+    elev = math.radians(elev_deg) * torch.cos(2 * math.pi * s + phase)
     rad = torch.full_like(s, radius)
     for k in range(1, 4):   # wobble: closed (periodic in s), decaying with the order
         a = torch.randn(4, dtype=F64, generator=g, device=device) / k
@@ -424,7 +428,7 @@ def make_scene(name: str, seed: int = 0, device="cpu", **overrides) -> Scene:
         keep = jj < n
         cam_i, cam_j = ii[keep], jj[keep]
     elif kind == "loop":
-        R, C = _cams_loop(n, cfg["laps"], g, device)
+        R, C = _cams_loop(n, cfg["laps"], g, device, elev_deg=cfg.get("elev_deg", 35.0))
         X = _ball_points(cfg["n_pts"], g, device)
         cam_i, cam_j = _loop_pairs(C, cfg["path_nb"], cfg["knn"] - 2 * cfg["path_nb"],
                                    n // (4 * cfg["laps"]))
@@ -597,3 +601,31 @@ def relative_rotations(sc: Scene, noise_deg: float = 1.0, outlier_frac: float = 
     ang[out, 0] = math.pi * torch.rand(int(out.sum()), dtype=F64, generator=g)
     Rrel = rotation_exp(axis * ang) @ Rrel
     return Rrel.numpy(), out.numpy()
+
+
+def fundamental_matrices(sc: Scene, noise: float = 1e-3, wrong_frac: float = 0.1, seed: int = 0, f=None):
+    """Fundamental matrices of the scene's image pairs as an upstream two-view estimation would
+    deliver them (the input of the focal-length vote): F = K_j^-T [t]_x R_ij K_i^-1 from the true
+    relative pose (R_ij = R_j R_i^T, t = R_j (c_i - c_j)), K = diag(f, f, 1) in pixels from the
+    image centre, with Gaussian noise of standard deviation `noise` added to every entry in
+    calibrated coordinates (where the entries share one scale) and a fraction `wrong_frac` of the
+    pairs replaced by random matrices. f: per-camera focal lengths (default: the scene's).
+    Returns (F (B, 3, 3) float64, wrong-pair mask)."""
+    g = torch.Generator(device="cpu")
+    g.manual_seed(int(seed) * 15485863 + 41)
+    R = sc.R_gt.detach().cpu().to(F64)
+    t = sc.t_gt.detach().cpu().to(F64)
+    C = -torch.einsum("nba,nb->na", R, t)
+    ci, cj = sc.cam_i.detach().cpu().long(), sc.cam_j.detach().cpu().long()
+    Rij = R[cj] @ R[ci].transpose(1, 2)
+    tij = torch.einsum("nab,nb->na", R[cj], C[ci] - C[cj])
+    E = _hat(tij) @ Rij
+    B = E.shape[0]
+    E = E + noise * torch.randn(B, 3, 3, dtype=F64, generator=g)
+    wrong = torch.rand(B, dtype=F64, generator=g) < wrong_frac
+    E[wrong] = torch.randn(int(wrong.sum()), 3, 3, dtype=F64, generator=g)
+    fv = torch.full((sc.n_cams,), float(sc.f), dtype=F64) if f is None else torch.as_tensor(f, dtype=F64)
+    one = torch.ones(B, dtype=F64)
+    si = torch.stack([fv[ci], fv[ci], one], 1)
+    sj = torch.stack([fv[cj], fv[cj], one], 1)
+    return (E / (sj[:, :, None] * si[:, None, :])).numpy(), wrong.numpy()

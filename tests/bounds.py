@@ -70,3 +70,31 @@ def grad_bound_ratio(g, ref, tol=1e-4, floor=1e-7):
     d = np.linalg.norm((np.asarray(g) - np.asarray(ref)).reshape(-1, 2, 3), axis=2)
     r = np.linalg.norm(np.asarray(ref).reshape(-1, 2, 3), axis=2)
     return float((d / (tol * r + floor * r.max(axis=0, keepdims=True))).max())
+
+
+def bf16_spacing(v):
+    """Distance between neighbouring BF16 values at |v| (8 significant bits)."""
+    a = np.maximum(np.abs(np.asarray(v, np.float64)), 1e-30)
+    return 2.0 ** (np.floor(np.log2(a)) - 7)
+
+
+def mlp_output_bound(L, params, X, dX):
+    """First-order bound, per row, on |p_gpu - p_oracle| for the network of the library's
+    numerics (BF16 inputs, weights and hidden activations, FP32 accumulation; L = oracle.learned).
+    The two sides may differ by (1) the input features before rounding (dX, per feature, from
+    the residual's FP32 error), which can move a BF16-rounded input by dX plus one BF16 spacing,
+    (2) the FP32 summation order of each dot product, which can move a BF16-rounded hidden
+    activation across one rounding boundary (one BF16 spacing), (3) the fast exponential and
+    reciprocal of the sigmoid (1e-6). Each is weighted by the oracle's own |dp/d.| at the row
+    (back-propagation through the BF16 network with its ReLU masks), and the sum is taken with a
+    factor 1.5 for the linearisation. Returns (p_oracle, bound)."""
+    p, (xb, z1, h1, z2, h2, z3, qp) = L.forward_bf16(params, X, keep=True)
+    s = p * (1.0 - p)
+    dh2 = s[:, None] * qp["W3"][:, 0][None, :]
+    dz2 = dh2 * (z2 > 0)
+    dh1 = dz2 @ qp["W2"].T
+    dz1 = dh1 * (z1 > 0)
+    dx = dz1 @ qp["W1"].T
+    b = (np.abs(dx) * (dX + bf16_spacing(xb))).sum(1)
+    b += (np.abs(dh1) * bf16_spacing(h1) * (h1 > 0)).sum(1) + (np.abs(dh2) * bf16_spacing(h2) * (h2 > 0)).sum(1)
+    return p, 1.5 * b + 1e-6

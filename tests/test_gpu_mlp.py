@@ -6,8 +6,9 @@ Tolerances: both sides use BF16 inputs, weights and hidden activations; they dif
 FP32 summation order of each dot product and, rarely, in a hidden activation that lands on
 the other side of a BF16 rounding boundary, which moves p by a few 1e-3 at most. Features
 are computed in FP32 on the GPU (FP64 in the oracle) from residuals that differ by the FP32
-forward error (2e-6, see test_gpu_parity), so they are compared where |eps| >= 1e-3 (a
-relative residual error below 2e-3) and up to BF16 rounding; the history is stored in FP16.
+forward error (2e-6, as in test_gpu_parity); every feature and every weight is held to a bound
+derived per point pair from those errors (see test_features_and_learned_weights_match_oracle);
+the history is stored in FP16.
 """
 import numpy as np
 import pytest
@@ -76,8 +77,40 @@ def test_training_reduces_loss():
     assert acc > 0.95
 
 
+def _feature_errors(L, e_now, e_prev16, pair_id, n_pairs, tau):
+    """Per point pair and feature, a bound on the FP32 error of the GPU's feature before BF16
+    rounding (the oracle computes it in FP64 from FP64 residuals): the residual's FP32 error
+    (2e-6 absolute) moves log(|e| + 1e-6) by at most 2e-6 / (|e| + 1e-6), the fast logarithm adds
+    3 ulp; an image pair's mean log and inlier fraction inherit the worst of their point pairs
+    (the fraction moves by one count for every residual within 2e-6 of tau); the FP16 history
+    moves by one FP16 spacing of the stored log."""
+    le = np.log(e_now + 1e-6)
+    dle = 2e-6 / (e_now + 1e-6) + 3 * 2.0 ** -23 * np.abs(le) + 1e-6
+    cnt = np.bincount(pair_id, minlength=n_pairs).astype(np.float64)
+    dmean = np.zeros(n_pairs)
+    np.maximum.at(dmean, pair_id, dle)
+    und = np.bincount(pair_id, weights=(np.abs(e_now - tau) <= 2e-6).astype(np.float64), minlength=n_pairs)
+    lp = np.log(e_prev16 + 1e-6)
+    dlp = 2.0 ** (np.floor(np.log2(np.maximum(np.abs(lp), 2.0 ** -14))) - 10) + 3e-6 / (e_prev16 + 1e-6) + 1e-6
+    dX = np.zeros((e_now.shape[0], 8))
+    dX[:, 0] = dle + 1e-6
+    dX[:, 1] = dle + dmean[pair_id] + 1e-5
+    dX[:, 2] = dlp + dle
+    dX[:, 4] = (und / cnt)[pair_id] + 1e-6
+    dX[:, 5] = 1e-6
+    dX[:, 6] = 1e-7
+    dX[:, 7] = dlp + 1e-6
+    return dX
+
+
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
-def test_features_and_learned_weights_match_oracle(storage):
+@pytest.mark.parametrize("fused", [False, True])
+def test_features_and_learned_weights_match_oracle(storage, fused):
+    """Every feature and every learned weight against the oracle, element by element: features
+    within their FP32 error bound plus one BF16 spacing; weights within the first-order bound of
+    tests/bounds.py (mlp_output_bound) carried through w = p / max(|e|, delta), plus the FP16
+    weight quantisation; the mask |e| <= tau_cap exact outside the residual's FP32 band."""
+    from bounds import bf16_spacing, mlp_output_bound
     sc = scenegen.make_scene("sphere128", seed=5)
     R0, t0 = sc.R_init.numpy(), sc.t_init.numpy()
     c0 = O.centres_from_poses(R0, t0)
@@ -86,37 +119,48 @@ def test_features_and_learned_weights_match_oracle(storage):
         _, d1, d2 = O.fp16_centroid_storage(prob, sc.x1.numpy(), sc.x2.numpy())
         prob = O.Problem(sc.n_cams, prob.cam_i, prob.cam_j, prob.pair_id, d1, d2)
     score = sc.score.numpy()
-    tau0, tau1 = 0.3, 0.2
+    tau0, tau1, delta = 0.3, 0.2, 1e-6
     pv = _params(7)
     net = fm.Mlp(pv)
     feats = torch.empty(sc.n_pp, 8, dtype=torch.bfloat16, device="cuda")
     with fm.Problem(R0, t0, sc.cam_i, sc.cam_j, sc.pair_id, sc.x1, sc.x2,
-                    options=fm.default_options(storage=storage)) as gp:
+                    options=fm.default_options(storage=storage, delta=delta)) as gp:
         gp.set_scores(score)
         gp.collect_features(tau0, 0, feats)          # round 0: history = current residuals
         f0 = feats.to(torch.float32).cpu().numpy()
         gp.step(5)                                    # move the poses
         R5, c5 = gp.get_params()
-        kept = gp.learned_weights(net, tau1, tau1, 1)  # round 1, history from round 0
+        if fused:                                     # round 1, history from round 0
+            kept = gp.step_learned(net, tau1, tau1, 1, 1, count=True)
+        else:
+            kept = gp.learned_weights(net, tau1, tau1, 1)
         w_gpu = gp.get_weights().astype(np.float64)
     e0 = np.abs(O.residuals(prob, R0, c0))
     e5 = np.abs(O.residuals(prob, R5, c5))
     sc16 = score.astype(np.float16).astype(np.float64)
+    # round-0 features: every one within its FP32 error plus one BF16 spacing
     F0 = L.features(e0, e0, sc16, prob.pair_id, prob.n_pairs, tau0, 0)
-    ok = e0 >= 1e-3
-    assert ok.mean() > 0.5
-    d = np.abs(f0 - L.bf16_round(F0))[ok]
-    tol = 2 ** -7 * np.abs(F0[ok]) + 2e-2
-    assert (d <= tol).mean() > 0.999
-    # learned weights at round 1 with the round-0 residuals as history (stored in FP16)
+    dX0 = _feature_errors(L, e0, e0, prob.pair_id, prob.n_pairs, tau0)
+    dX0[:, 2] = 2 * (2e-6 / (e0 + 1e-6) + 3 * 2.0 ** -23 * np.abs(np.log(e0 + 1e-6)) + 1e-6)
+    dX0[:, 7] = dX0[:, 0]
+    assert (np.abs(f0 - L.bf16_round(F0)) <= dX0 + bf16_spacing(F0) + 1e-12).all()
+    # round-1 weights with the round-0 residuals as history (stored in FP16)
     hist = np.log(e0 + 1e-6).astype(np.float16).astype(np.float64)
-    F1 = L.features(e5, np.exp(hist) - 1e-6, sc16, prob.pair_id, prob.n_pairs, tau1, 1)
-    w_or, p_or = L.learned_weights(L.unflatten(pv.astype(np.float64)), e5, F1, 1e-6, tau_cap=tau1)
-    ok1 = (e5 >= 1e-3) & (e5 <= 0.9 * tau1)
-    rel = np.abs(w_gpu[ok1] - w_or[ok1]) / np.maximum(w_or[ok1], 1e-12)
-    assert np.median(rel) < 1e-2
-    assert (rel < 0.1).mean() > 0.99
-    assert abs(kept - (e5 <= tau1).sum()) <= 0.001 * sc.n_pp
+    e_prev = np.exp(hist) - 1e-6
+    F1 = L.features(e5, e_prev, sc16, prob.pair_id, prob.n_pairs, tau1, 1)
+    dX1 = _feature_errors(L, e5, e0, prob.pair_id, prob.n_pairs, tau1)
+    params = L.unflatten(pv.astype(np.float64))
+    p_or, dp = mlp_output_bound(L, params, F1, dX1)
+    m = np.maximum(e5, delta)
+    w_or = np.where(e5 <= tau1, p_or / m, 0.0)
+    dw = dp / m + p_or * 2e-6 / (m * m) + 4 * 2.0 ** -24 * w_or
+    if storage == "fp16":
+        dw += 2.0 ** -11 * w_or + 2.0 ** -24
+    decided = np.abs(e5 - tau1) > 2e-6
+    assert ((w_gpu > 0) == (e5 <= tau1))[decided].all()
+    err = np.abs(w_gpu - w_or)[decided]
+    assert (err <= dw[decided]).all(), (err / dw[decided]).max()
+    assert abs(kept - (e5 <= tau1).sum()) <= int((~decided).sum())
 
 
 def test_trained_network_gains_over_plain_reweighting():
@@ -142,3 +186,30 @@ def test_trained_network_gains_over_plain_reweighting():
                 net.close()
             err[arm] = float(metrics.rotation_error_deg(gp.get_poses()[0], Rg).mean())
     assert err["learned"] < 0.5 * err["irls"], err
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_fused_learned_round_is_bit_identical(storage):
+    # fm_step_learned = fm_learned_weights + fm_step with the learned reweighting inside the first
+    # pass; two rounds, so the second one reads the residual history the first one wrote
+    sc = scenegen.make_scene("sphere128", seed=9)
+    R0, t0 = sc.R_init.numpy(), sc.t_init.numpy()
+    net = fm.Mlp(_params(11))
+    res = []
+    for fused in (False, True):
+        with fm.Problem(R0, t0, sc.cam_i, sc.cam_j, sc.pair_id, sc.x1, sc.x2,
+                        options=fm.default_options(storage=storage)) as gp:
+            gp.set_scores(sc.score.numpy())
+            kept = []
+            for rnd, tau in enumerate((0.3, 0.2)):
+                if fused:
+                    kept.append(gp.step_learned(net, tau, tau, rnd, 7, count=True))
+                else:
+                    kept.append(gp.learned_weights(net, tau, tau, rnd))
+                    gp.step(7)
+            res.append((kept, gp.get_weights(), gp.get_params(), gp.last_loss(), gp.get_state()[2]))
+    (k0, w0, p0, l0, s0), (k1, w1, p1, l1, s1) = res
+    assert k0 == k1 and s0 == s1 == 14 and l0 == l1
+    np.testing.assert_array_equal(w0, w1)
+    np.testing.assert_array_equal(p0[0], p1[0])
+    np.testing.assert_array_equal(p0[1], p1[1])

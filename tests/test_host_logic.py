@@ -58,20 +58,22 @@ def test_refine_learned_reweights_with_the_network_every_round(quadratic):
     p = learned.refine_learned(Recorder(), net, sch, quadratic=quadratic)
     assert p.calls[0] == ("reset_history",)
     body = p.calls[1:]
-    step = ["preaggregate", "step_quadratic"] if quadratic else ["step"]
-    per_round = 2 + len(step)
+    per_round = 4 if quadratic else 2
     assert len(body) == per_round * sch.rounds
     for r in range(sch.rounds):
         c = body[per_round * r: per_round * (r + 1)]
         tau = O.threshold_schedule(r, 0.3, 0.02, 0.5)
-        assert c[0][0] == "learned_weights" and c[0][1] is net
-        assert c[0][2:] == (pytest.approx(tau), pytest.approx(tau), r)
-        assert c[1][0] == "set_learning_rate"
-        assert [x[0] for x in c[2:]] == step
-        assert c[-1][-1] == 7
+        assert c[0] == ("set_learning_rate", pytest.approx(2e-3 * 0.9 ** r), pytest.approx(5e-2 * 0.9 ** r))
+        if quadratic:
+            assert c[1][0] == "learned_weights" and c[1][1] is net
+            assert c[1][2:] == (pytest.approx(tau), pytest.approx(tau), r)
+            assert c[2] == ("preaggregate",) and c[3] == ("step_quadratic", 7)
+        else:   # the learned reweighting fused into the round's first pass
+            assert c[1][0] == "step_learned" and c[1][1] is net
+            assert c[1][2:] == (pytest.approx(tau), pytest.approx(tau), r, 7)
     # a resumed run keeps the residual history
     p = learned.refine_learned(Recorder(), net, sch, first_round=2)
-    assert p.calls[0][0] == "learned_weights"
+    assert [c[0] for c in p.calls[:2]] == ["set_learning_rate", "step_learned"]
 
 
 def test_schedule_threshold_matches_the_oracle_rule():

@@ -89,10 +89,33 @@ def test_loop_scene_closes_and_links_laps():
     z = R[:, 2, :]                                    # viewing direction in world coordinates
     miss = np.linalg.norm(np.cross(z, -C), axis=1)   # distance of the origin from the axis
     assert (miss < 1.0).all()
-    # 8 neighbours along the path and 12 views of other laps for every camera
+    # 8 neighbours along the path and 12 views of other laps (more than a quarter lap away
+    # along the path) for every camera
     steps = np.abs(ci - cj)
     steps = np.minimum(steps, n - steps)
-    far = steps > n // 20
+    far = steps > n // (4 * 20)
     deg_far = np.bincount(np.concatenate([ci[far], cj[far]]), minlength=n)
     assert deg_far.min() >= 12 and far.mean() > 0.4
     assert ((steps <= 4) | far).all()
+    # the height sweeps +-70 degrees of elevation, so the laps cover the view sphere's band
+    elev = np.degrees(np.arcsin(C[:, 2] / np.linalg.norm(C, axis=1)))
+    assert elev.min() < -60 and elev.max() > 60
+    # initial centres moved by 10% of the median pair baseline
+    base = np.median(np.linalg.norm(C[ci] - C[cj], axis=1))
+    C0 = O.centres_from_poses(sc.R_init.numpy(), sc.t_init.numpy())
+    np.testing.assert_allclose(np.linalg.norm(C0 - C, axis=1), 0.1 * base, rtol=1e-9)
+
+
+def test_fundamental_matrices_annihilate_true_matches():
+    # noise-free matches of a noise-free scene satisfy x2^T F x1 = 0 in pixels from the image
+    # centre, and the wrong-pair fraction is as asked
+    sc = scenegen.make_scene("ring16", seed=3, sigma_px=0.0, outlier=0.0)
+    F, wrong = scenegen.fundamental_matrices(sc, noise=0.0, wrong_frac=0.0)
+    assert not wrong.any()
+    p1 = np.concatenate([sc.x1.numpy().astype(np.float64) * sc.f, np.ones((sc.n_pp, 1))], 1)
+    p2 = np.concatenate([sc.x2.numpy().astype(np.float64) * sc.f, np.ones((sc.n_pp, 1))], 1)
+    Fp = F[sc.pair_id.numpy()]
+    r = np.einsum("pa,pab,pb->p", p2, Fp, p1) / (np.linalg.norm(Fp, axis=(1, 2)) * sc.f * sc.f)
+    assert np.abs(r).max() < 1e-6
+    _, wrong = scenegen.fundamental_matrices(scenegen.make_scene("sphere128", seed=3), wrong_frac=0.1)
+    assert abs(wrong.mean() - 0.1) < 0.03
