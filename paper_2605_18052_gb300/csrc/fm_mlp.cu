@@ -18,6 +18,7 @@
 #include <cstring>
 #include <string>
 
+#include "fm_tcgen05.cuh"
 #include "fm_walk.cuh"
 
 namespace fm {
@@ -469,15 +470,366 @@ k_learned_loss(DevProblem d, const float *master, const __nv_bfloat16 *wbf, floa
     if (threadIdx.x == 0 && cta_kept) atomicAdd(d.counter, (unsigned long long)cta_kept);
 }
 
+// ---- the learned reweighting on the fifth-generation tensor cores (tcgen05) ---------------------
+// A CTA is one warpgroup (4 warps); each warp streams its own warp range as in the other passes,
+// and for every group of 32 * PPL point pairs per warp the warpgroup's 128 x PPL rows go through
+// the network as MMAs of M = 128 rows with FP32 accumulators in TMEM (k = the lane's k-th point
+// pair of the group, one MMA row block per k):
+//   L1  D1[k] (128 x 32) = A1[k] (128 x 16: 8 features, three 1s, 5 zeros) . B1^T
+//        B1 (32 x 16) = W1^T with b1 in its columns 8..10 as three BF16 parts (hi + mid + lo = b1)
+//   L2  D2[k] (128 x 32) = A2[k] (128 x 48: bf16(relu(D1)), three 1s, zeros) . B2^T (W2^T, b2 parts)
+//   L3  D3[k] (128 x 16, column 0 used) = A3[k] (A2's layout, from D2) . B3^T (row 0: W3, b3 parts)
+// so the biases are added inside the FP32 accumulation and every row's epilogue is one TMEM load,
+// one ReLU-and-round instruction per two values and four 16-byte shared-memory stores. One thread
+// issues the MMAs and commits them to an mbarrier; the warpgroup waits on it (bounded: a wait that
+// runs out records ERR_NONFINITE and the warpgroup leaves the loop together).
+// Footprint (the pass is bound by the latency of the MMA round trips, so what matters is how many
+// row blocks an SM keeps in flight): D1, D2 and D3 of row block k share TMEM columns 32 k .. 32 k
+// + 31 (each layer's result is read before the next layer's MMA is issued), 64 columns per CTA;
+// A1 lives inside A2's buffer: the features take A2's first K core matrix and layer 1 reads its
+// second K core matrix from A2's fifth (the constant bias inputs), through the descriptor's
+// leading byte offset.
+// FUSE: also accumulate the loss + adjoint sums with the new weights (the round's first pass).
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_COLS = 64;
+constexpr int TC_K1 = 16, TC_K2 = 48;      // padded K of layer 1 and of layers 2 and 3
+constexpr long long TC_WAIT_CYCLES = 2000000000LL;   // about one second
+
+struct TcSmem {
+    alignas(128) unsigned char a2[2][128 * TC_K2 * 2];
+    alignas(128) unsigned char b1[32 * TC_K1 * 2];
+    alignas(128) unsigned char b2[32 * TC_K2 * 2];
+    alignas(128) unsigned char b3[16 * TC_K2 * 2];
+    alignas(8) uint64_t mbar;
+    uint32_t tmem;
+    int fail;
+    unsigned kept;
+};
+
+__device__ __forceinline__ void put_bf16(unsigned char *base, uint32_t r, uint32_t k, uint32_t kp, float v) {
+    *reinterpret_cast<__nv_bfloat16 *>(base + tc_offset(r, k, kp)) = __float2bfloat16_rn(v);
+}
+
+// v = hi + mid + lo with three BF16 values (exact for FP32 v up to the last bit of lo)
+__device__ __forceinline__ void bf16_split3(float v, float &hi, float &mid, float &lo) {
+    hi = __bfloat162float(__float2bfloat16_rn(v));
+    mid = __bfloat162float(__float2bfloat16_rn(v - hi));
+    lo = v - hi - mid;
+}
+
+// the network's B operands and the constant columns of the A operands, by the whole CTA
+__device__ __forceinline__ void tc_setup(TcSmem &sm, const float *master, const __nv_bfloat16 *wbf) {
+    const int tid = threadIdx.x;
+    const __nv_bfloat16 *W1 = wbf, *W2 = wbf + MLP_IN * MLP_H, *W3 = W2 + MLP_H * MLP_H;
+    for (int i = tid; i < 32 * TC_K1; i += TC_THREADS) {
+        const int n = i / TC_K1, k = i % TC_K1;
+        float v = 0.f;
+        if (k < MLP_IN) v = __bfloat162float(W1[k * MLP_H + n]);
+        else if (k < MLP_IN + 3) {
+            float h, m, l;
+            bf16_split3(master[MLP_OFF_B1 + n], h, m, l);
+            v = k == MLP_IN ? h : (k == MLP_IN + 1 ? m : l);
+        }
+        put_bf16(sm.b1, n, k, TC_K1, v);
+    }
+    for (int i = tid; i < 32 * TC_K2; i += TC_THREADS) {
+        const int n = i / TC_K2, k = i % TC_K2;
+        float v = 0.f;
+        if (k < MLP_H) v = __bfloat162float(W2[k * MLP_H + n]);
+        else if (k < MLP_H + 3) {
+            float h, m, l;
+            bf16_split3(master[MLP_OFF_B2 + n], h, m, l);
+            v = k == MLP_H ? h : (k == MLP_H + 1 ? m : l);
+        }
+        put_bf16(sm.b2, n, k, TC_K2, v);
+    }
+    for (int i = tid; i < 16 * TC_K2; i += TC_THREADS) {
+        const int n = i / TC_K2, k = i % TC_K2;
+        float v = 0.f;
+        if (n == 0 && k < MLP_H) v = __bfloat162float(W3[k]);
+        else if (n == 0 && k < MLP_H + 3) {
+            float h, m, l;
+            bf16_split3(master[MLP_OFF_B3], h, m, l);
+            v = k == MLP_H ? h : (k == MLP_H + 1 ? m : l);
+        }
+        put_bf16(sm.b3, n, k, TC_K2, v);
+    }
+    // A2 columns 32..47: three 1s (the bias inputs of every layer) and zeros
+    for (int i = tid; i < 2 * 128 * (TC_K2 - MLP_H); i += TC_THREADS) {
+        const int kk = i / (128 * (TC_K2 - MLP_H)), rem = i % (128 * (TC_K2 - MLP_H));
+        const int r = rem / (TC_K2 - MLP_H), k = MLP_H + rem % (TC_K2 - MLP_H);
+        put_bf16(sm.a2[kk], r, k, TC_K2, k < MLP_H + 3 ? 1.f : 0.f);
+    }
+}
+
+// bf16(relu(x)) of 32 accumulator columns into row `row` of an A operand (K padded to TC_K2)
+__device__ __forceinline__ void tc_relu_row(unsigned char *a, int row, const uint32_t (&acc)[32]) {
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {
+        uint4 v;
+        v.x = pack_relu_bf16(__uint_as_float(acc[8 * kb + 0]), __uint_as_float(acc[8 * kb + 1]));
+        v.y = pack_relu_bf16(__uint_as_float(acc[8 * kb + 2]), __uint_as_float(acc[8 * kb + 3]));
+        v.z = pack_relu_bf16(__uint_as_float(acc[8 * kb + 4]), __uint_as_float(acc[8 * kb + 5]));
+        v.w = pack_relu_bf16(__uint_as_float(acc[8 * kb + 6]), __uint_as_float(acc[8 * kb + 7]));
+        *reinterpret_cast<uint4 *>(a + tc_offset(row, 8 * kb, TC_K2)) = v;
+    }
+}
+
+// all warpgroup threads: make the A rows visible to the tensor core and hand over to the issuer;
+// returns whether an earlier wait ran out (then everybody leaves)
+__device__ __forceinline__ bool tc_handover(TcSmem &sm) {
+    fence_smem_async();
+    tc_fence_before_sync();
+    named_sync(1, TC_THREADS);
+    return sm.fail != 0;
+}
+
+__device__ __forceinline__ void tc_wait(TcSmem &sm, uint32_t &phase) {
+    if (!mbar_wait(smem_addr(&sm.mbar), phase, TC_WAIT_CYCLES)) sm.fail = 1;
+    phase ^= 1u;
+    tc_fence_after_sync();
+}
+
+template <int STORE, bool FUSE>
+__global__ void __launch_bounds__(TC_THREADS, 5)
+k_learned_tc(DevProblem d, const float *master, const __nv_bfloat16 *wbf, float tau, float tau_cap, int round,
+             int hist_valid) {
+    using F = Fmt<STORE>;
+    constexpr int PPL = F::PPL;
+    constexpr int GROUP = 32 * PPL;
+    constexpr int NG = WR / GROUP;
+    __shared__ TcSmem sm;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int row = 32 * wid + lane;
+    if (wid == 0) {
+        tmem_alloc(smem_addr(&sm.tmem), TC_COLS);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&sm.mbar), 1);
+        sm.fail = 0;
+        sm.kept = 0;
+    }
+    tc_setup(sm, master, wbf);
+    pdl_wait();     // pair geometry and statistics of this pass
+    pdl_trigger();
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tm = sm.tmem + ((uint32_t)(32 * wid) << 16);   // this warp's TMEM lanes
+    const uint32_t id1 = tc_idesc_bf16(128, 32), id3 = tc_idesc_bf16(128, 16);
+    // operand descriptors (loop-invariant; K slice sl of layers 2 and 3 adds sl * 2 * TC_LBO to
+    // the start address field, i.e. sl * 16 in 16-byte units)
+    const uint64_t dA1[2] = {tc_desc(smem_addr(sm.a2[0]), TC_K2 * 16, 4 * TC_LBO),
+                             tc_desc(smem_addr(sm.a2[1]), TC_K2 * 16, 4 * TC_LBO)};
+    const uint64_t dA2[2] = {tc_desc(smem_addr(sm.a2[0]), TC_K2 * 16), tc_desc(smem_addr(sm.a2[1]), TC_K2 * 16)};
+    const uint64_t dB1 = tc_desc(smem_addr(sm.b1), TC_K1 * 16), dB2 = tc_desc(smem_addr(sm.b2), TC_K2 * 16),
+                   dB3 = tc_desc(smem_addr(sm.b3), TC_K2 * 16);
+    constexpr uint64_t SLICE = (2 * TC_LBO) >> 4;
+    uint32_t phase = 0;
+
+    const int r = blockIdx.x * 4 + wid;
+    const bool r_ok = r < d.n_ranges;
+    const float log_tau = __logf(tau), delta = (float)d.delta, wscale = d.w_scale, round_f = round * 0.1f;
+    const int64_t p_begin = (int64_t)r * WR;
+    const int64_t p_end = r_ok ? min(p_begin + (int64_t)WR, d.n_pp) : p_begin;
+    int seg = r_ok ? d.range_pair[r] : 0;
+    int64_t seg_end = r_ok ? d.pair_off[seg + 1] : 0;
+    LossBody<MODE_LOSS_IRLS> loss(d);
+    unsigned kept = 0;
+    const uint64_t pol = evict_first_policy();
+    // the keypoints, scores and history of the next group are loaded one group ahead, so their
+    // latency overlaps the current group's MMAs
+    typename F::Raw nraw;
+    unsigned nsc = 0u, nhi = 0u;
+    auto fetch = [&](int64_t gq) {
+        nraw = F::load(d, gq, false, pol);
+        if (PPL == 2) {
+            nsc = *reinterpret_cast<const unsigned *>(d.score + gq);
+            nhi = *reinterpret_cast<const unsigned *>(d.le_hist + gq);
+        } else {
+            nsc = __half_as_ushort(d.score[gq]);
+            nhi = __half_as_ushort(d.le_hist[gq]);
+        }
+    };
+    if (p_begin < p_end) fetch(p_begin + lane * PPL);
+    for (int g = 0; g < NG; ++g) {
+        const int64_t gb = p_begin + (int64_t)g * GROUP;
+        const bool active = gb < p_end;   // warp-uniform
+        const int64_t q0 = gb + lane * PPL;
+        typename F::Raw raw = nraw;
+        const unsigned csc = nsc, chi = nhi;
+        if (gb + GROUP < p_end) fetch(q0 + GROUP);
+        float sco[PPL], lp[PPL], e[PPL], le[PPL];
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) sco[k] = lp[k] = e[k] = le[k] = 0.f;
+        int seg0 = seg;
+        int64_t seg0_end = seg_end;
+        // ---- phase A: features of the lane's point pairs into A1[k], row `row`
+        uint4 feat[PPL];
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) feat[k] = make_uint4(0u, 0u, 0u, 0u);
+        if (active) {
+            if (PPL == 2) {
+                const float2 sv = __half22float2(*reinterpret_cast<const __half2 *>(&csc));
+                const float2 hv = __half22float2(*reinterpret_cast<const __half2 *>(&chi));
+                sco[0] = sv.x;
+                sco[PPL - 1] = sv.y;
+                lp[0] = hv.x;
+                lp[PPL - 1] = hv.y;
+            } else {
+                sco[0] = __half2float(__ushort_as_half((unsigned short)csc));
+                lp[0] = __half2float(__ushort_as_half((unsigned short)chi));
+            }
+            const int64_t g_end = min(gb + GROUP, p_end);
+            float E[9];
+            load_E(d.geo, seg, E);
+            float4 st = reinterpret_cast<const float4 *>(d.pstat)[seg];
+            int64_t lo = gb;
+            while (true) {
+                const int64_t hi = min(seg_end, p_end);
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) {
+                    const int64_t q = q0 + k;
+                    if (q >= lo && q < hi) {
+                        float x1, y1, x2, y2, unused;
+                        F::get(raw, k, x1, y1, x2, y2, unused);
+                        e[k] = epi(E, x1, y1, x2, y2);
+                        le[k] = __logf(fabsf(e[k]) + LOG_FLOOR);
+                        const float lpk = hist_valid ? lp[k] : le[k];
+                        feat[k] = make_uint4(pack_bf16(le[k] - log_tau, le[k] - st.x),
+                                             pack_bf16(lpk - le[k], sco[k]), pack_bf16(st.y, st.z),
+                                             pack_bf16(round_f, lpk - log_tau));
+                    }
+                }
+                if (seg_end >= g_end) break;
+                lo = seg_end;
+                ++seg;
+                seg_end = d.pair_off[seg + 1];
+                load_E(d.geo, seg, E);
+                st = reinterpret_cast<const float4 *>(d.pstat)[seg];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) *reinterpret_cast<uint4 *>(sm.a2[k] + tc_offset(row, 0, TC_K2)) = feat[k];
+        // ---- layer 1
+        if (tc_handover(sm)) break;
+        if (threadIdx.x == 0) {
+            tc_fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < PPL; ++k)
+                tc_mma_bf16(sm.tmem + 32 * k, dA1[k], dB1, id1, 0u);
+            tc_commit(smem_addr(&sm.mbar));
+        }
+        tc_wait(sm, phase);
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            uint32_t acc[32];
+            tmem_ld32(tm + 32 * k, acc);
+            tc_relu_row(sm.a2[k], row, acc);
+        }
+        // ---- layer 2
+        if (tc_handover(sm)) break;
+        if (threadIdx.x == 0) {
+            tc_fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < PPL; ++k)
+#pragma unroll
+                for (int sl = 0; sl < TC_K2 / 16; ++sl)
+                    tc_mma_bf16(sm.tmem + 32 * k, dA2[k] + sl * SLICE, dB2 + sl * SLICE, id1, sl > 0 ? 1u : 0u);
+            tc_commit(smem_addr(&sm.mbar));
+        }
+        tc_wait(sm, phase);
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            uint32_t acc[32];
+            tmem_ld32(tm + 32 * k, acc);
+            tc_relu_row(sm.a2[k], row, acc);
+        }
+        // ---- layer 3
+        if (tc_handover(sm)) break;
+        if (threadIdx.x == 0) {
+            tc_fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < PPL; ++k)
+#pragma unroll
+                for (int sl = 0; sl < TC_K2 / 16; ++sl)
+                    tc_mma_bf16(sm.tmem + 32 * k, dA2[k] + sl * SLICE, dB3 + sl * SLICE, id3, sl > 0 ? 1u : 0u);
+            tc_commit(smem_addr(&sm.mbar));
+        }
+        tc_wait(sm, phase);
+        float z[PPL];
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) z[k] = __uint_as_float(tmem_ld1(tm + 32 * k));
+        tc_fence_before_sync();
+        if (!active) continue;
+        // ---- weights, history, kept count
+        float w[PPL];
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            const float pk = __frcp_rn(1.f + __expf(-z[k]));
+            const float ae = fabsf(e[k]);
+            const bool in = q0 + k < p_end && ae <= tau_cap;
+            const float wf = in ? learned_weight(pk, ae, delta) : 0.f;
+            w[k] = STORE == FM_STORE_FP32 ? wf : __half2float(__float2half_rn(wf * wscale));
+            kept += in ? 1u : 0u;
+        }
+        if (STORE == FM_STORE_FP32) {
+            static_cast<float *>(d.w)[q0] = w[0];
+            if (q0 < p_end) d.le_hist[q0] = __float2half_rn(le[0]);
+        } else {
+            reinterpret_cast<__half2 *>(d.w)[q0 >> 1] = __floats2half2_rn(w[0], w[PPL - 1]);
+            const __half2 hv = __floats2half2_rn(le[0], le[PPL - 1]);
+            if (q0 + 1 < p_end) reinterpret_cast<__half2 *>(d.le_hist)[q0 >> 1] = hv;
+            else if (q0 < p_end) d.le_hist[q0] = __low2half(hv);
+        }
+        if (!FUSE) continue;
+        // ---- phase B: loss and adjoint sums with the new weights
+        int sb = seg0;
+        int64_t sb_end = seg0_end, lo = gb;
+        while (true) {
+            const int64_t hi = min(sb_end, p_end);
+#pragma unroll
+            for (int k = 0; k < PPL; ++k) {
+                const int64_t q = q0 + k;
+                if (q >= lo && q < hi) {
+                    float x1, y1, x2, y2, unused;
+                    F::get(raw, k, x1, y1, x2, y2, unused);
+                    loss.point(k, e[k], x1, y1, x2, y2, w[k]);
+                }
+            }
+            if (sb == seg) break;
+            loss.segment_end(sb, r, lane, false);
+            lo = sb_end;
+            ++sb;
+            sb_end = d.pair_off[sb + 1];
+        }
+    }
+    if (FUSE && r_ok) loss.segment_end(seg, r, lane, true);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    if (lane == 0 && kept) atomicAdd(&sm.kept, kept);
+    tc_fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (sm.kept) atomicAdd(d.counter, (unsigned long long)sm.kept);
+        if (sm.fail) atomicOr(d.err, ERR_NONFINITE);
+    }
+    if (wid == 0) {
+        tc_fence_after_sync();
+        tmem_dealloc(sm.tmem, TC_COLS);
+    }
+}
+
 static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 void launch_learned_loss(const DevProblem &d, const float *master, const __nv_bfloat16 *wbf, float tau,
                          float tau_cap, int round, int hist_valid, cudaStream_t s, bool pdl) {
-    const dim3 grid(blocks_for(d.n_ranges, CTA_WARPS)), block(CTA_WARPS * 32);
+    const dim3 grid(blocks_for(d.n_ranges, TC_THREADS / 32)), block(TC_THREADS);
     if (d.storage == FM_STORE_FP32)
-        launch_k(k_learned_loss<FM_STORE_FP32>, grid, block, s, pdl, d, master, wbf, tau, tau_cap, round, hist_valid);
+        launch_k(k_learned_tc<FM_STORE_FP32, true>, grid, block, s, pdl, d, master, wbf, tau, tau_cap, round, hist_valid);
     else
-        launch_k(k_learned_loss<FM_STORE_FP16>, grid, block, s, pdl, d, master, wbf, tau, tau_cap, round, hist_valid);
+        launch_k(k_learned_tc<FM_STORE_FP16, true>, grid, block, s, pdl, d, master, wbf, tau, tau_cap, round, hist_valid);
 }
 
 void launch_pair_stats(const DevProblem &d, float tau, cudaStream_t s) {
@@ -489,11 +841,11 @@ void launch_pair_stats(const DevProblem &d, float tau, cudaStream_t s) {
 
 void launch_learned_weights(const DevProblem &d, const float *master, const __nv_bfloat16 *wbf, float tau,
                             float tau_cap, int round, int hist_valid, cudaStream_t s) {
-    const int grid = blocks_for(d.n_ranges, CTA_WARPS);
+    const dim3 grid(blocks_for(d.n_ranges, TC_THREADS / 32)), block(TC_THREADS);
     if (d.storage == FM_STORE_FP32)
-        k_learned<FM_STORE_FP32, false><<<grid, CTA_WARPS * 32, 0, s>>>(d, master, wbf, tau, tau_cap, round, hist_valid, nullptr);
+        launch_k(k_learned_tc<FM_STORE_FP32, false>, grid, block, s, false, d, master, wbf, tau, tau_cap, round, hist_valid);
     else
-        k_learned<FM_STORE_FP16, false><<<grid, CTA_WARPS * 32, 0, s>>>(d, master, wbf, tau, tau_cap, round, hist_valid, nullptr);
+        launch_k(k_learned_tc<FM_STORE_FP16, false>, grid, block, s, false, d, master, wbf, tau, tau_cap, round, hist_valid);
 }
 
 void launch_collect_features(const DevProblem &d, float tau, int round, int hist_valid,

@@ -83,9 +83,9 @@ class Scene:
 #               log-normal counts (median 2k, cap 20k, ~3e6 point pairs), 15% outliers, 1 px.
 #   traj1000  : 1,000 cameras along a smooth random trajectory, 500k points, 20 neighbours
 #               (~1e4 pairs), log-normal counts (~5e7 point pairs), 20% outliers, 1 px.
-#   traj1000_o30 : traj1000 with 30% outliers (learned-weight evaluation scene).
-#   sphere128_o30 : sphere128 with 30% outliers (the learned weights' training distribution;
-#               evaluated on seeds outside the training seeds 1000-1199).
+#   traj1000_o30 : traj1000 with 30% outliers.
+#   sphere128_o30 : sphere128 with 30% outliers (the learned weights' training shape with twice
+#               the outliers; evaluated on seeds outside the training seeds 1000-1199).
 #   traj4000  : 4,000 cameras, 2M points, 25 neighbours (~5e4 pairs), Pareto(1.5) counts
 #               capped at 50k (~1.5e8 point pairs), 25% outliers, 1.5 px.
 #   loop1000  : 1,000 cameras along a random smooth closed trajectory that winds 20 times

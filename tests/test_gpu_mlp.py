@@ -164,7 +164,7 @@ def test_features_and_learned_weights_match_oracle(storage, fused):
 
 
 def test_trained_network_gains_over_plain_reweighting():
-    # held-out scene of the training distribution (128-camera sphere, 30% outliers; the
+    # held-out scene of the training shape (128-camera sphere, here with 30% outliers; the
     # network was trained on seeds 1000-1199): after the same 10 rounds the learned weights
     # leave a clearly smaller rotation error than the hard IRLS mask
     import os
