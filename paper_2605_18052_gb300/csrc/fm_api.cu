@@ -2,9 +2,11 @@
 // optimiser iteration, error reporting. Every per-point-pair pass is a kernel in
 // fm_kernels.cu / fm_layout.cu; this file only allocates, validates host arguments and
 // launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -42,15 +44,15 @@ struct fm_problem {
     cudaStream_t user = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaGraphExec_t graph = nullptr;      // one iteration
-    cudaGraphExec_t graph8 = nullptr;     // eight chained iterations
+    // CUDA graphs of chained iterations, by length n (key n) and of chains whose first pass is
+    // fused with the reweighting (key -n)
+    std::map<int, cudaGraphExec_t> chains;
     bool timing = false;
     int hist_valid = 0;                   // d.le_hist holds a previous reweighting's residuals
     double lr_focal = 1e-3;               // Adam step size of rho = log(f0/f)
     bool quad_alloc = false;              // d.qslots, d.quad, d.pair_rec allocated
     bool quad_valid = false;              // d.quad holds the form of the current weights
     cudaGraphExec_t qgraph = nullptr, qgraph8 = nullptr;  // quadratic-path iterations
-    cudaGraphExec_t rgraph = nullptr;     // one iteration whose pass is fused with the reweighting
     // timing events per timed pass (fm_pass_time), pairs (start, end)
     std::vector<cudaEvent_t> tev[FM_NUM_PASSES];
     size_t tev_used[FM_NUM_PASSES] = {};
@@ -179,28 +181,27 @@ void time_end(fm_problem *p, int pass, cudaStream_t s) {
     p->tev_used[pass] += 2;
 }
 
-// one optimiser iteration (three launches, chained with programmatic dependent launch);
-// `first` = the iteration does not follow another one in this chain; `reweight`: the round's
-// reweighting fused into this iteration's pass
+// one optimiser iteration, chained with programmatic dependent launch: the pass over the point
+// pairs, then the camera step, which also writes the geometry records of the new poses; the
+// first iteration of a chain computes the geometry with a pair-setup launch, later ones find
+// it written and their pass finishes the previous step's loss total and step count.
+// `reweight`: the round's reweighting fused into this iteration's pass (always a first one).
 void enqueue_iteration(fm_problem *p, cudaStream_t s, bool timed, bool first, bool reweight = false) {
-    launch_pair_setup(p->d, s, true, !first);
+    if (first) launch_pair_setup(p->d, s, true, false);
     const int pass = reweight ? FM_PASS_STREAM_REWEIGHT : FM_PASS_STREAM_LOSS;
-    if (timed && time_begin(p, pass, s)) {
-        if (reweight) launch_stream_reweight(p->d, s, false);
-        else launch_stream_loss(p->d, s, false);
-        time_end(p, pass, s);
-        launch_camera_step(p->d, true, s, false);
-        return;
-    }
-    if (reweight) launch_stream_reweight(p->d, s, true);
-    else launch_stream_loss(p->d, s, true);
-    launch_camera_step(p->d, true, s, true);
+    const bool t = timed && time_begin(p, pass, s);
+    if (reweight) launch_stream_reweight(p->d, s, !t);
+    else launch_stream_loss(p->d, s, !t, !first);
+    if (t) time_end(p, pass, s);
+    launch_camera_step(p->d, true, s, !t, true);
 }
 
-// `iters` chained iterations and the closing finalize launch; `quad`: fused steps on the
-// pre-aggregated quadratic form (one launch per iteration), alternating between the two
-// camera-record buffers; after an odd count the finalize launch copies the records back
-void enqueue_iterations(fm_problem *p, cudaStream_t s, bool timed, int iters, bool quad = false) {
+// `iters` chained iterations and the closing finalize launch (reweight: the first pass fused
+// with the round's reweighting); `quad`: fused steps on the pre-aggregated quadratic form (one
+// launch per iteration), alternating between the two camera-record buffers; after an odd count
+// the finalize launch copies the records back
+void enqueue_iterations(fm_problem *p, cudaStream_t s, bool timed, int iters, bool quad = false,
+                        bool reweight = false) {
     if (quad) {
         for (int it = 0; it < iters; ++it) {
             const bool even = (it & 1) == 0;
@@ -210,20 +211,15 @@ void enqueue_iterations(fm_problem *p, cudaStream_t s, bool timed, int iters, bo
         launch_finalize_n(p->d, iters, (iters & 1) ? p->d.cam_alt : nullptr, s, true);
         return;
     }
-    for (int it = 0; it < iters; ++it) enqueue_iteration(p, s, timed, it == 0);
+    for (int it = 0; it < iters; ++it) enqueue_iteration(p, s, timed, it == 0, reweight && it == 0);
     launch_finalize(p->d, true, s, !timed);
 }
 
-// a graph of `iters` chained iterations (reweight: one iteration fused with the reweighting)
+// a graph of `iters` chained iterations (reweight: the first pass fused with the reweighting)
 fm_status build_graph(fm_problem *p, int iters, cudaGraphExec_t *out, bool quad = false, bool reweight = false) {
     cudaGraph_t g = nullptr;
     FM_CUDA(cudaStreamBeginCapture(p->s, cudaStreamCaptureModeThreadLocal));
-    if (reweight) {
-        enqueue_iteration(p, p->s, false, true, true);
-        launch_finalize(p->d, true, p->s, true);
-    } else {
-        enqueue_iterations(p, p->s, false, iters, quad);
-    }
+    enqueue_iterations(p, p->s, false, iters, quad, reweight);
     cudaError_t e = cudaStreamEndCapture(p->s, &g);
     if (e != cudaSuccess) return fail(FM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(out, g, 0);
@@ -235,15 +231,37 @@ fm_status build_graph(fm_problem *p, int iters, cudaGraphExec_t *out, bool quad 
     return FM_OK;
 }
 
+// n chained iterations as CUDA graphs of whole chains (one pair-setup and one finalize launch
+// per chain), built on first use and kept by length; a chain runs at most CHAIN_MAX
+// iterations, and once CHAIN_CACHE lengths are kept, new lengths run as chains of 8 and 1.
+// reweight: the first pass is fused with the round's reweighting.
+fm_status launch_chains(fm_problem *p, int n, bool reweight) {
+    constexpr int CHAIN_MAX = 64;
+    constexpr size_t CHAIN_CACHE = 24;
+    for (int left = n; left > 0;) {
+        int len = std::min(left, CHAIN_MAX);
+        if (!p->chains.count(reweight ? -len : len) && p->chains.size() >= CHAIN_CACHE) len = len >= 8 ? 8 : 1;
+        const int key = reweight ? -len : len;
+        auto it = p->chains.find(key);
+        if (it == p->chains.end()) {
+            cudaGraphExec_t g = nullptr;
+            if (fm_status st = build_graph(p, len, &g, false, reweight)) return st;
+            it = p->chains.emplace(key, g).first;
+        }
+        FM_CUDA(cudaGraphLaunch(it->second, p->s));
+        left -= len;
+        reweight = false;
+    }
+    return FM_OK;
+}
+
 void free_problem(fm_problem *p) {
     if (!p) return;
     if (p->s) cudaStreamSynchronize(p->s);
     for (void *a : p->allocs) cudaFree(a);
-    if (p->graph) cudaGraphExecDestroy(p->graph);
-    if (p->graph8) cudaGraphExecDestroy(p->graph8);
+    for (auto &kv : p->chains) cudaGraphExecDestroy(kv.second);
     if (p->qgraph) cudaGraphExecDestroy(p->qgraph);
     if (p->qgraph8) cudaGraphExecDestroy(p->qgraph8);
-    if (p->rgraph) cudaGraphExecDestroy(p->rgraph);
     for (auto &ev : p->tev)
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
@@ -302,6 +320,7 @@ fm_status create_impl(fm_problem *p, int32_t n_cams, const double *R, const doub
     FM_CUDA(dalloc(p, &d.hyper, 8));
     FM_CUDA(dalloc(p, &d.step, 1));
     FM_CUDA(dalloc(p, &d.cam, (size_t)CAMREC * n_cams));
+    FM_CUDA(dalloc(p, &d.pair_cnt, (size_t)n_pairs));
     FM_CUDA(dalloc(p, &d.cen, (size_t)n_cams));
     FM_CUDA(dalloc(p, &d.cam_i, (size_t)n_pairs));
     FM_CUDA(dalloc(p, &d.cam_j, (size_t)n_pairs));
@@ -351,6 +370,7 @@ fm_status create_impl(fm_problem *p, int32_t n_cams, const double *R, const doub
     FM_CUDA(cudaMemsetAsync(d.step, 0, sizeof(long long), p->s));
     FM_CUDA(cudaMemsetAsync(d.cen, 0, sizeof(float2) * n_cams, p->s));
     FM_CUDA(cudaMemsetAsync(d.geo, 0, sizeof(float) * GEO * n_pairs, p->s));
+    FM_CUDA(cudaMemsetAsync(d.pair_cnt, 0, sizeof(unsigned) * n_pairs, p->s));
     FM_CUDA(cudaMemcpyAsync(d.cam_i, cam_i, sizeof(int) * n_pairs, cudaMemcpyHostToDevice, p->s));
     FM_CUDA(cudaMemcpyAsync(d.cam_j, cam_j, sizeof(int) * n_pairs, cudaMemcpyHostToDevice, p->s));
     FM_CUDA(cudaMemcpyAsync(d.cam_off, cam_off.data(), sizeof(int) * (n_cams + 1), cudaMemcpyHostToDevice, p->s));
@@ -818,18 +838,8 @@ FM_API fm_status fm_step(fm_problem *p, int32_t n_iters) {
     if (p->timing || !p->opt.use_graph) {
         enqueue_iterations(p, p->s, p->timing, n_iters);
         FM_CUDA(cudaGetLastError());
-    } else {
-        if (!p->graph) {
-            fm_status st = build_graph(p, 1, &p->graph);
-            if (st != FM_OK) return st;
-        }
-        if (n_iters >= 8 && !p->graph8) {
-            fm_status st = build_graph(p, 8, &p->graph8);
-            if (st != FM_OK) return st;
-        }
-        int left = n_iters;
-        for (; left >= 8; left -= 8) FM_CUDA(cudaGraphLaunch(p->graph8, p->s));
-        for (; left > 0; --left) FM_CUDA(cudaGraphLaunch(p->graph, p->s));
+    } else if (fm_status st = launch_chains(p, n_iters, false)) {
+        return st;
     }
     FM_CUDA(join_out(p));
     return FM_OK;
@@ -846,20 +856,13 @@ FM_API fm_status fm_step_irls(fm_problem *p, double tau, int32_t n_iters, int64_
     FM_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(unsigned long long), p->s));
     p->quad_valid = false;
     if (p->timing || !p->opt.use_graph) {
-        enqueue_iteration(p, p->s, p->timing, true, true);
-        launch_finalize(p->d, true, p->s, !p->timing);
+        enqueue_iterations(p, p->s, p->timing, n_iters, false, true);
         FM_CUDA(cudaGetLastError());
-    } else {
-        if (!p->rgraph) {
-            fm_status st = build_graph(p, 1, &p->rgraph, false, true);
-            if (st != FM_OK) return st;
-        }
-        FM_CUDA(cudaGraphLaunch(p->rgraph, p->s));
+    } else if (fm_status st = launch_chains(p, n_iters, true)) {
+        return st;
     }
     unsigned long long cnt = 0;
     if (n_active) FM_CUDA(cudaMemcpyAsync(&cnt, p->d.counter, sizeof cnt, cudaMemcpyDeviceToHost, p->s));
-    if (n_iters > 1)
-        if (fm_status st = fm_step(p, n_iters - 1)) return st;
     if (n_active) {
         if (fm_status st = check_device_errors(p)) return st;
         *n_active = (int64_t)cnt;

@@ -90,6 +90,7 @@ struct DevProblem {
     float *qslots;          // (n_pairs + n_ranges) x QSLOT
     float *quad;            // n_pairs x QREC: c0, g0(9), M(36), e0(9), pad
     float *cam_alt;         // n_cams x CAMREC: second camera-record buffer of the fused step
+    unsigned *pair_cnt;     // per pair: cameras updated by camera steps with the geometry phase
 };
 
 // c0 = sum w eps0^2, g0 = sum w eps0 a (9), M = the 36 distinct entries of W = sum w a a^T
@@ -144,8 +145,10 @@ int camera_step_blocks(const DevProblem &d);
 // factors applied to the raw sums of the loss (Sum w eps^2 or Sum |eps|, weights stored as
 // w * s): gradient 2/(Z s) and loss 1/(Z s) for IRLS, 1/Z for L1
 void loss_scales(const DevProblem &d, float &gscale, float &lscale);
-// streaming loss + adjoint: per (image pair, CTA range) partial sums in d.slots
-void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl = false);
+// streaming loss + adjoint: per (image pair, CTA range) partial sums in d.slots; after_step:
+// the previous kernel was an optimiser camera step whose loss total and step count this
+// launch finishes
+void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl = false, bool after_step = false);
 // the same pass fused with the IRLS reweighting at threshold d.hyper[6]; kept count in d.counter
 void launch_stream_reweight(const DevProblem &d, cudaStream_t s, bool pdl = false);
 void launch_combine(const DevProblem &d, cudaStream_t s);
@@ -154,8 +157,9 @@ void launch_gather(const DevProblem &d, bool count_step, cudaStream_t s);
 // exponential map, camera record; the last block sums the loss and advances the step count
 // Adam step of every camera with the gradient in d.grad (FP64, n_cams x 6); advances the step
 void launch_apply_gradient(const DevProblem &d, cudaStream_t s);
-// apply = false computes the gradient and loss only (no Adam step, no step count)
-void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl = false);
+// apply = false computes the gradient and loss only (no Adam step, no step count); next_geo
+// (with apply, when d.pair_cnt is allocated): also the geometry records of the new poses
+void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl = false, bool next_geo = false);
 void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s);
 void launch_residuals(const DevProblem &d, float *out_sorted, cudaStream_t s);
 

@@ -15,10 +15,14 @@
 
 namespace fm {
 
+// prev_blocks > 0: this pass follows an optimiser camera step with that many blocks (which
+// also wrote this pass's geometry records); block 0 finishes that step's loss total and step
+// count first.
 template <int STORE, int MODE>
-__global__ void __launch_bounds__(CTA_WARPS * 32, 4) k_stream_loss(DevProblem d) {
+__global__ void __launch_bounds__(CTA_WARPS * 32, 4) k_stream_loss(DevProblem d, int prev_blocks) {
     pdl_wait();     // pair geometry of this pass
     pdl_trigger();  // the per-camera step may be scheduled once the last wave has started
+    if (prev_blocks > 0 && blockIdx.x == 0) finish_step(d, prev_blocks, 1);
     const int r = blockIdx.x * CTA_WARPS + (threadIdx.x >> 5);
     if (r >= d.n_ranges) return;
     LossBody<MODE> body(d);
@@ -327,19 +331,27 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather(DevProblem d, int cou
 // Adam update (FP32 moments), R <- Exp(phi) R and Gram-Schmidt re-orthonormalisation in FP64,
 // the centre update in FP64 and the new camera record. Keeping the FP64 work lane-parallel
 // matters on GB300, whose FP64 pipe charges a whole warp instruction per operation.
-// Geometry comes from the pair records of pair_setup, never from another camera's record,
-// which another block may be updating. The loss of a pair is counted by its first camera
-// only; each block writes the FP64 sum of its cameras' losses to cam_loss[block], and the
-// next kernel (pair setup or the finalize kernel) adds them up and advances the step count.
+// Geometry comes from the pair records, never from another camera's record, which another
+// block may be updating. The loss of a pair is counted by its first camera only; each block
+// writes the FP64 sum of its cameras' losses to cam_loss[block], and the next kernel (the next
+// pass, pair setup or the finalize kernel) adds them up and advances the step count.
+// Phase 3 (next_geo, with apply): the geometry records of the new poses, so the next pass
+// needs no pair-setup launch. Each camera's warp counts its image pairs in d.pair_cnt (one
+// acquire-release atomic per (pair, camera); every such step adds 2 to each pair's count); the
+// camera that finds an odd count is the pair's second, both records are then written, and it
+// computes the pair's record. A record is overwritten only after both of its readers in this
+// launch (the pair's two cameras) have passed phase 1, and the pass that read E'_n has
+// completed before this kernel's wait.
 template <bool FOCAL>
 __global__ void __launch_bounds__(STEP_CAMS * 32, 4)
-k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
+k_camera_step(DevProblem d, float gscale, float lscale, int apply, int next_geo) {
     constexpr int NV = FOCAL ? STEP_VALS : STEP_VALS - 1;   // sums carried per camera
     __shared__ float s_hi[STEP_VALS][STEP_CAMS], s_lo[STEP_VALS][STEP_CAMS];
     __shared__ int4 s_item[STEP_CAMS][32];
     __shared__ __align__(16) float s_geo[STEP_CAMS][32][GEO];
     __shared__ float s_mv[STEP_CAMS][12];     // Adam m (6) and v (6) of the block's cameras
     __shared__ double s_Rc[STEP_CAMS][12];    // R (9) and c (3) of the block's cameras
+    __shared__ float s_R32[STEP_CAMS][9];     // their FP32 record rotations
     __shared__ double s_hyper[6];   // lr_rot, lr_c, beta1, beta2, eps, lr_focal
     __shared__ double s_loss[STEP_CAMS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -351,6 +363,7 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
             if (cam0 + cc < d.n_cams) {
                 s_mv[cc][q] = q < 6 ? d.m[(size_t)(cam0 + cc) * 6 + q] : d.v[(size_t)(cam0 + cc) * 6 + q - 6];
                 s_Rc[cc][q] = q < 9 ? d.R[(size_t)(cam0 + cc) * 9 + q] : d.c[(size_t)(cam0 + cc) * 3 + q - 9];
+                if (q < 9) s_R32[cc][q] = d.cam[(size_t)(cam0 + cc) * CAMREC + q];
             }
         }
         if (threadIdx.x < 6) s_hyper[threadIdx.x] = d.hyper[threadIdx.x];
@@ -426,9 +439,10 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
     if (warp == 0 && lane < STEP_CAMS) {
         const int kc = blockIdx.x * STEP_CAMS + lane;
         const double bl = kc < d.n_cams
-            ? camera_update<FOCAL>(d, kc, &s_hi[0][lane], &s_lo[0][lane], STEP_CAMS, s_mv[lane], s_Rc[lane], s_hyper,
-                            t_step, apply, d.cam + (size_t)kc * CAMREC)
+            ? camera_update<FOCAL>(d, kc, &s_hi[0][lane], &s_lo[0][lane], STEP_CAMS, s_mv[lane], s_Rc[lane],
+                                   s_R32[lane], s_hyper, t_step, apply, d.cam + (size_t)kc * CAMREC)
             : 0.0;
+        if (apply && next_geo) __threadfence();   // the record reaches L2 before any count below
         s_loss[lane] = bl;
         __syncwarp(0xffu);
         if (lane == 0) {
@@ -436,6 +450,14 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply) {
 #pragma unroll
             for (int q = 0; q < STEP_CAMS; ++q) b += s_loss[q];
             d.cam_loss[blockIdx.x] = b;
+        }
+    }
+    if (!(apply && next_geo)) return;
+    __syncthreads();   // the block's new records are written
+    if (k < d.n_cams) {
+        for (int e = e_begin + lane; e < e_end; e += 32) {
+            const int n = d.cam_ent[e] >> 1;
+            if (atomic_add_acq_rel(d.pair_cnt + n, 1u) & 1u) pair_geometry(d, n, d.cam_i[n], d.cam_j[n]);
         }
     }
 }
@@ -530,14 +552,16 @@ void launch_finalize_n(const DevProblem &d, int count, const float *copy_src, cu
     launch_k(k_finalize, dim3(1), dim3(FIN_THREADS), s, pdl, d, camera_step_blocks(d), count);
 }
 
-void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl) {
+void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl, bool after_step) {
+    static_assert(CTA_WARPS * 32 == FIN_THREADS, "block 0 of the pass finishes a step");
     const dim3 grid(blocks_for(d.n_ranges, CTA_WARPS)), block(CTA_WARPS * 32);
+    const int prev = after_step ? camera_step_blocks(d) : 0;
     if (d.storage == FM_STORE_FP32) {
-        if (d.loss == FM_LOSS_IRLS) launch_k(k_stream_loss<FM_STORE_FP32, MODE_LOSS_IRLS>, grid, block, s, pdl, d);
-        else launch_k(k_stream_loss<FM_STORE_FP32, MODE_LOSS_L1>, grid, block, s, pdl, d);
+        if (d.loss == FM_LOSS_IRLS) launch_k(k_stream_loss<FM_STORE_FP32, MODE_LOSS_IRLS>, grid, block, s, pdl, d, prev);
+        else launch_k(k_stream_loss<FM_STORE_FP32, MODE_LOSS_L1>, grid, block, s, pdl, d, prev);
     } else {
-        if (d.loss == FM_LOSS_IRLS) launch_k(k_stream_loss<FM_STORE_FP16, MODE_LOSS_IRLS>, grid, block, s, pdl, d);
-        else launch_k(k_stream_loss<FM_STORE_FP16, MODE_LOSS_L1>, grid, block, s, pdl, d);
+        if (d.loss == FM_LOSS_IRLS) launch_k(k_stream_loss<FM_STORE_FP16, MODE_LOSS_IRLS>, grid, block, s, pdl, d, prev);
+        else launch_k(k_stream_loss<FM_STORE_FP16, MODE_LOSS_L1>, grid, block, s, pdl, d, prev);
     }
 }
 
@@ -580,15 +604,16 @@ void launch_apply_gradient(const DevProblem &d, cudaStream_t s) {
     k_bump_step<<<1, 1, 0, s>>>(d);
 }
 
-void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl) {
+void launch_camera_step(const DevProblem &d, bool apply, cudaStream_t s, bool pdl, bool next_geo) {
     float gscale, lscale;
     loss_scales(d, gscale, lscale);
+    const int ng = next_geo && d.pair_cnt ? 1 : 0;
     if (d.refine_focal)
         launch_k(k_camera_step<true>, dim3(blocks_for(d.n_cams, STEP_CAMS)), dim3(STEP_CAMS * 32), s, pdl, d,
-                 gscale, lscale, apply ? 1 : 0);
+                 gscale, lscale, apply ? 1 : 0, ng);
     else
         launch_k(k_camera_step<false>, dim3(blocks_for(d.n_cams, STEP_CAMS)), dim3(STEP_CAMS * 32), s, pdl, d,
-                 gscale, lscale, apply ? 1 : 0);
+                 gscale, lscale, apply ? 1 : 0, ng);
 }
 
 void launch_irls_weights(const DevProblem &d, float tau, cudaStream_t s) {

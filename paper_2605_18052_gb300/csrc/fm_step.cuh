@@ -83,6 +83,32 @@ __device__ __forceinline__ double rsqrt64(double x) {
     return y;
 }
 
+// Exp(phi) - I = a K + b K^2 (K = [phi]_x) in FP32. A rotation increment is small, so its
+// FP32 relative error (a few ulp) is an absolute error of a few 1e-7 |phi|, the same order as
+// that of phi itself, which Adam computes in FP32. For |phi| < 0.1 the Taylor series of a and b
+// through the t^6 terms (truncation below 1e-13); otherwise sin and b = 2 sin^2(t/2) / t^2.
+__device__ __forceinline__ void so3_exp_minus_identity(const float *phi, float *A) {
+    const float th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
+    float a, b;
+    if (th2 < 0.01f) {
+        a = 1.f - th2 * (1.f / 6.f) * (1.f - th2 * (1.f / 20.f) * (1.f - th2 * (1.f / 42.f)));
+        b = 0.5f * (1.f - th2 * (1.f / 12.f) * (1.f - th2 * (1.f / 30.f) * (1.f - th2 * (1.f / 56.f))));
+    } else {
+        const float th = sqrtf(th2);
+        const float sh = sinf(0.5f * th);
+        a = sinf(th) / th;
+        b = 2.f * sh * sh / th2;
+    }
+    const float K[9] = {0.f, -phi[2], phi[1], phi[2], 0.f, -phi[0], -phi[1], phi[0], 0.f};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float k2 = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+            A[3 * r + c] = a * K[3 * r + c] + b * k2;
+        }
+}
+
 // Gram-Schmidt on the rows: r0 normalised, r1 orthogonalised and normalised, r2 = r0 x r1
 __device__ __forceinline__ void orthonormalize_rows(double *R) {
     const double n0 = rsqrt64(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
@@ -219,43 +245,57 @@ __device__ __forceinline__ void warp_two_sum_reduce(float *hi, float *lo) {
         }
 }
 
-// Phase 2 of a step for camera kc, one lane: the FP64 sum of the gradient's hi + lo parts, then
-// either the gradient is written (apply = 0) or one Adam step (FP32 moments) with the FP64
-// exponential map, re-orthonormalisation and centre update, and the new camera record at
-// rec_out. hi/lo hold STEP_VALS values (6 pose gradient components, the loss, the keypoint-
-// scale gradient) `stride` apart; mv = the camera's Adam m (6) and v (6); Rc = its R (9) and
-// c (3); hyper = lr_rot, lr_c, beta1, beta2, eps, lr_focal. With focal refinement rho = log s
-// takes its own Adam step (gradient s dL/ds). Returns the camera's loss share.
+// Phase 2 of a step for camera kc, one lane. apply = 0: the gradient (FP64 sum of its hi + lo
+// parts) and the focal gradient are written, nothing else. apply = 1: one Adam step (FP32
+// moments) and the new pose: R <- R + (Exp(phi) - I) R and c <- c + delta_c in FP64, where the
+// small increment (Exp(phi) - I) R is formed in FP32 from the camera's FP32 record rotation R32
+// (its error, a few 1e-7 |phi|, is of the order of phi's own FP32 error), then Gram-Schmidt on
+// the rows in FP64 and the new camera record at rec_out. hi/lo hold STEP_VALS values (6 pose
+// gradient components, the loss, the keypoint-scale gradient) `stride` apart; mv = the
+// camera's Adam m (6) and v (6); Rc = its R (9) and c (3) in FP64; hyper = lr_rot, lr_c,
+// beta1, beta2, eps, lr_focal. With focal refinement rho = log s takes its own Adam step
+// (gradient s dL/ds). Returns the camera's loss share.
+// GB300 executes FP64 on a narrow pipe at whole-warp cost per instruction, and every block of a
+// step reaches this phase at the same moment, so the update keeps its FP64 work to the state
+// itself (about 90 operations: the two sums, the re-orthonormalisation and the record).
 template <bool FOCAL>
 __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, const float *hi, const float *lo,
-                                                int stride, const float *mv, const double *Rc,
+                                                int stride, const float *mv, const double *Rc, const float *R32,
                                                 const double *hyper, long long t_step, int apply,
                                                 float *rec_out) {
-    double g[6];
-    bool ok = isfinite(hi[6 * stride]);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        g[q] = (double)hi[q * stride] + (double)lo[q * stride];
-        ok = ok && isfinite(g[q]);
-    }
-    if (!ok) atomicOr(d.err, ERR_NONFINITE);
     const double bl = (double)hi[6 * stride] + (double)lo[6 * stride];
     const double s_cur = camera_scale(d, kc);
     const double g_rho = FOCAL ? s_cur * ((double)hi[7 * stride] + (double)lo[7 * stride]) : 0.0;
     if (!apply) {
+        bool ok = isfinite(hi[6 * stride]);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) d.grad[(size_t)kc * 6 + q] = g[q];
+        for (int q = 0; q < 6; ++q) {
+            const double g = (double)hi[q * stride] + (double)lo[q * stride];
+            ok = ok && isfinite(g);
+            d.grad[(size_t)kc * 6 + q] = g;
+        }
+        if (!ok) atomicOr(d.err, ERR_NONFINITE);
         if (d.grad_rho) d.grad_rho[kc] = g_rho;
         return bl;
     }
+    // the FP32 gradient: hi is the rounded value of hi + lo (TwoSum keeps |lo| within half an
+    // ulp of hi), so hi + lo in FP32 is the same number the FP64 sum would round to
+    float gq[6];
+    bool ok = isfinite(hi[6 * stride]);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        gq[q] = hi[q * stride] + lo[q * stride];
+        ok = ok && isfinite(gq[q]);
+    }
+    if (!ok) atomicOr(d.err, ERR_NONFINITE);
     double s_new = s_cur;
     const float b1 = (float)hyper[2], b2 = (float)hyper[3], eps = (float)hyper[4];
     const float lr_r = (float)hyper[0], lr_c = (float)hyper[1];
     const float bc1 = 1.f - powf(b1, (float)t_step), bc2 = 1.f - powf(b2, (float)t_step);
     if (FOCAL) {
-        const float gq = (float)g_rho;
-        const float mo = b1 * d.rho_m[kc] + (1.f - b1) * gq;
-        const float vo = b2 * d.rho_v[kc] + (1.f - b2) * gq * gq;
+        const float g1 = (float)g_rho;
+        const float mo = b1 * d.rho_m[kc] + (1.f - b1) * g1;
+        const float vo = b2 * d.rho_v[kc] + (1.f - b2) * g1 * g1;
         d.rho_m[kc] = mo;
         d.rho_v[kc] = vo;
         const double r = d.rho[kc] - (double)((float)hyper[5] * (mo / bc1) / (sqrtf(vo / bc2) + eps));
@@ -263,31 +303,29 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
         d.grad_rho[kc] = g_rho;
         s_new = exp(r);
     }
-    double dl[6];
-    float mo[6], vo[6];
+    float dl[6], mo[6], vo[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-        const float gq = (float)g[q];
-        mo[q] = b1 * mv[q] + (1.f - b1) * gq;
-        vo[q] = b2 * mv[6 + q] + (1.f - b2) * gq * gq;
-        dl[q] = (double)(-(q < 3 ? lr_r : lr_c) * (mo[q] / bc1) / (sqrtf(vo[q] / bc2) + eps));
+        mo[q] = b1 * mv[q] + (1.f - b1) * gq[q];
+        vo[q] = b2 * mv[6 + q] + (1.f - b2) * gq[q] * gq[q];
+        dl[q] = -(q < 3 ? lr_r : lr_c) * (mo[q] / bc1) / (sqrtf(vo[q] / bc2) + eps);
     }
-    double Ex[9], Rn[9], cn[3];
-    expmap64(dl, Ex);
+    float A[9];
+    so3_exp_minus_identity(dl, A);
+    double Rn[9], cn[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            Rn[3 * r + c] = Ex[3 * r] * Rc[c] + Ex[3 * r + 1] * Rc[3 + c] + Ex[3 * r + 2] * Rc[6 + c];
+            Rn[3 * r + c] = Rc[3 * r + c] + (double)(A[3 * r] * R32[c] + A[3 * r + 1] * R32[3 + c] + A[3 * r + 2] * R32[6 + c]);
     orthonormalize_rows(Rn);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) cn[q] = Rc[9 + q] + dl[3 + q];
+    for (int q = 0; q < 3; ++q) cn[q] = Rc[9 + q] + (double)dl[3 + q];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
         const size_t o = (size_t)kc * 6 + q;
         d.m[o] = mo[q];
         d.v[o] = vo[q];
-        d.grad[o] = g[q];
     }
 #pragma unroll
     for (int q = 0; q < 9; ++q) d.R[(size_t)kc * 9 + q] = Rn[q];

@@ -139,6 +139,13 @@ __device__ __forceinline__ float epi(const float *E, float x1, float y1, float x
 // set by the residual's FP32 error.
 __device__ __forceinline__ float irls_weight(float a, float delta) { return __fdividef(1.0f, fmaxf(a, delta)); }
 
+// *p += v at GPU scope with acquire-release semantics; returns the old value
+__device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // ---- the streaming walk ------------------------------------------------------------------------
 // Warp `r` streams point pairs [r*WR, min((r+1)*WR, n_pp)). Lane l of group g handles PPL
 // consecutive point pairs at g*32*PPL + l*PPL, so every load instruction of the warp reads one
@@ -260,10 +267,12 @@ struct LossBody {
 };
 
 // ---- per pair: relative pose and folded essential matrix ------------------------------------------
-// camera record: R (9), centre as hi (3) + lo (3) floats, s = scale of the normalised keypoints
+// camera record: R (9), centre as hi (3) + lo (3) floats, s = scale of the normalised keypoints.
+// Read at L2 (ld.global.cg): a record may have been written by another block of the same
+// launch (the camera step's geometry phase), and L1 is not coherent across SMs.
 __device__ __forceinline__ void load_camrec(const float *rec, float *R, float *hi, float *lo, float &s) {
     const float4 *v = reinterpret_cast<const float4 *>(rec);
-    const float4 a = v[0], b = v[1], c = v[2], e = v[3];
+    const float4 a = __ldcg(v), b = __ldcg(v + 1), c = __ldcg(v + 2), e = __ldcg(v + 3);
     R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w;
     R[4] = b.x; R[5] = b.y; R[6] = b.z; R[7] = b.w;
     R[8] = c.x;
