@@ -316,7 +316,7 @@ fm_status create_impl(fm_problem *p, int32_t n_cams, const double *R, const doub
     FM_CUDA(dalloc(p, &d.rho_m, (size_t)n_cams));
     FM_CUDA(dalloc(p, &d.rho_v, (size_t)n_cams));
     d.refine_focal = p->opt.refine_focal;
-    FM_CUDA(dalloc(p, &d.cam_loss, (size_t)camera_step_blocks(d)));
+    FM_CUDA(dalloc(p, &d.cam_loss, (size_t)n_cams));
     FM_CUDA(dalloc(p, &d.hyper, 8));
     FM_CUDA(dalloc(p, &d.step, 1));
     FM_CUDA(dalloc(p, &d.cam, (size_t)CAMREC * n_cams));

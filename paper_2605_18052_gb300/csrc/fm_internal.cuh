@@ -68,7 +68,7 @@ struct DevProblem {
     int refine_focal;
     float *m, *v;
     long long *step;
-    double *cam_loss;        // per-block loss partials of the fused step kernel
+    double *cam_loss;        // per-camera loss shares of the last optimiser step (FP64)
     float *cam;             // camera records
     float2 *cen;            // per-camera centroids (zeros for FP32 storage)
     int *cam_i, *cam_j, *pair_off, *range_pair;

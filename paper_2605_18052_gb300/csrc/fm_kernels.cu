@@ -15,14 +15,14 @@
 
 namespace fm {
 
-// prev_blocks > 0: this pass follows an optimiser camera step with that many blocks (which
-// also wrote this pass's geometry records); block 0 finishes that step's loss total and step
-// count first.
+// prev_loss > 0: this pass follows an optimiser camera step (which also wrote this pass's
+// geometry records); block 0 first finishes that step's loss total (over prev_loss per-camera
+// shares) and step count.
 template <int STORE, int MODE>
-__global__ void __launch_bounds__(CTA_WARPS * 32, 4) k_stream_loss(DevProblem d, int prev_blocks) {
+__global__ void __launch_bounds__(CTA_WARPS * 32, 4) k_stream_loss(DevProblem d, int prev_loss) {
     pdl_wait();     // pair geometry of this pass
     pdl_trigger();  // the per-camera step may be scheduled once the last wave has started
-    if (prev_blocks > 0 && blockIdx.x == 0) finish_step(d, prev_blocks, 1);
+    if (prev_loss > 0 && blockIdx.x == 0) finish_step(d, prev_loss, 1);
     const int r = blockIdx.x * CTA_WARPS + (threadIdx.x >> 5);
     if (r >= d.n_ranges) return;
     LossBody<MODE> body(d);
@@ -176,14 +176,14 @@ __global__ void k_cam_prep(DevProblem d) {
     write_camrec(d.cam + (size_t)k * CAMREC, d.R + 9 * (size_t)k, d.c + 3 * (size_t)k, camera_scale(d, k));
 }
 
-// prev_blocks > 0: this pass follows an optimiser step whose camera-step kernel had that many
-// blocks; block 0 (with 256 threads) finishes that step's loss total and step count.
-__global__ void __launch_bounds__(256) k_pair_setup(DevProblem d, int prev_blocks) {
+// prev_loss > 0: this pass follows an optimiser step with that many per-camera loss shares;
+// block 0 (with 256 threads) finishes that step's loss total and step count.
+__global__ void __launch_bounds__(256) k_pair_setup(DevProblem d, int prev_loss) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = n < d.n_pairs ? d.cam_i[n] : 0, j = n < d.n_pairs ? d.cam_j[n] : 0;
     pdl_wait();     // camera records of the previous step
     pdl_trigger();
-    if (prev_blocks > 0 && blockIdx.x == 0) finish_step(d, prev_blocks, 1);
+    if (prev_loss > 0 && blockIdx.x == 0) finish_step(d, prev_loss, 1);
     if (n >= d.n_pairs) return;
     pair_geometry(d, n, i, j);
 }
@@ -332,9 +332,9 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather(DevProblem d, int cou
 // the centre update in FP64 and the new camera record. Keeping the FP64 work lane-parallel
 // matters on GB300, whose FP64 pipe charges a whole warp instruction per operation.
 // Geometry comes from the pair records, never from another camera's record, which another
-// block may be updating. The loss of a pair is counted by its first camera only; each block
-// writes the FP64 sum of its cameras' losses to cam_loss[block], and the next kernel (the next
-// pass, pair setup or the finalize kernel) adds them up and advances the step count.
+// block may be updating. The loss of a pair is counted by its first camera only; each camera's
+// FP64 loss share goes to cam_loss[camera], and the next kernel (the next pass, pair setup or
+// the finalize kernel) adds them up in a fixed order and advances the step count.
 // Phase 3 (next_geo, with apply): the geometry records of the new poses, so the next pass
 // needs no pair-setup launch. Each camera's warp counts its image pairs in d.pair_cnt (one
 // acquire-release atomic per (pair, camera); every such step adds 2 to each pair's count); the
@@ -353,7 +353,6 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply, int next_geo)
     __shared__ double s_Rc[STEP_CAMS][12];    // R (9) and c (3) of the block's cameras
     __shared__ float s_R32[STEP_CAMS][9];     // their FP32 record rotations
     __shared__ double s_hyper[6];   // lr_rot, lr_c, beta1, beta2, eps, lr_focal
-    __shared__ double s_loss[STEP_CAMS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = blockIdx.x * STEP_CAMS + warp;
     {
@@ -443,14 +442,7 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply, int next_geo)
                                    s_R32[lane], s_hyper, t_step, apply, d.cam + (size_t)kc * CAMREC)
             : 0.0;
         if (apply && next_geo) __threadfence();   // the record reaches L2 before any count below
-        s_loss[lane] = bl;
-        __syncwarp(0xffu);
-        if (lane == 0) {
-            double b = 0.0;
-#pragma unroll
-            for (int q = 0; q < STEP_CAMS; ++q) b += s_loss[q];
-            d.cam_loss[blockIdx.x] = b;
-        }
+        if (kc < d.n_cams) d.cam_loss[kc] = bl;
     }
     if (!(apply && next_geo)) return;
     __syncthreads();   // the block's new records are written
@@ -513,10 +505,10 @@ __global__ void k_apply_gradient(DevProblem d) {
 __global__ void k_bump_step(DevProblem d) { *d.step += 1; }
 
 // closes a chain of steps: loss of the last step and `count` steps added to the step count
-__global__ void __launch_bounds__(FIN_THREADS) k_finalize(DevProblem d, int n_blocks, int count) {
+__global__ void __launch_bounds__(FIN_THREADS) k_finalize(DevProblem d, int n_loss, int count) {
     pdl_wait();
     pdl_trigger();
-    finish_step(d, n_blocks, count);
+    finish_step(d, n_loss, count);
 }
 
 // camera records copied back from the alternate buffer (one float4 per thread)
@@ -537,8 +529,7 @@ void launch_cam_prep(const DevProblem &d, cudaStream_t s) {
 }
 
 void launch_pair_setup(const DevProblem &d, cudaStream_t s, bool pdl, bool after_step) {
-    launch_k(k_pair_setup, dim3(blocks_for(d.n_pairs, 256)), dim3(256), s, pdl, d,
-             after_step ? camera_step_blocks(d) : 0);
+    launch_k(k_pair_setup, dim3(blocks_for(d.n_pairs, 256)), dim3(256), s, pdl, d, after_step ? d.n_cams : 0);
 }
 
 void launch_finalize(const DevProblem &d, bool count_step, cudaStream_t s, bool pdl) {
@@ -549,13 +540,13 @@ void launch_finalize_n(const DevProblem &d, int count, const float *copy_src, cu
     if (copy_src)
         launch_k(k_copy_records, dim3(blocks_for((int64_t)d.n_cams * (CAMREC / 4), 256)), dim3(256), s, pdl, d,
                  reinterpret_cast<const float4 *>(copy_src));
-    launch_k(k_finalize, dim3(1), dim3(FIN_THREADS), s, pdl, d, camera_step_blocks(d), count);
+    launch_k(k_finalize, dim3(1), dim3(FIN_THREADS), s, pdl, d, d.n_cams, count);
 }
 
 void launch_stream_loss(const DevProblem &d, cudaStream_t s, bool pdl, bool after_step) {
     static_assert(CTA_WARPS * 32 == FIN_THREADS, "block 0 of the pass finishes a step");
     const dim3 grid(blocks_for(d.n_ranges, CTA_WARPS)), block(CTA_WARPS * 32);
-    const int prev = after_step ? camera_step_blocks(d) : 0;
+    const int prev = after_step ? d.n_cams : 0;
     if (d.storage == FM_STORE_FP32) {
         if (d.loss == FM_LOSS_IRLS) launch_k(k_stream_loss<FM_STORE_FP32, MODE_LOSS_IRLS>, grid, block, s, pdl, d, prev);
         else launch_k(k_stream_loss<FM_STORE_FP32, MODE_LOSS_L1>, grid, block, s, pdl, d, prev);

@@ -171,7 +171,6 @@ k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gs
     __shared__ double s_Rc[STEP_CAMS][12];
     __shared__ float s_R32[STEP_CAMS][9];     // the cameras' FP32 record rotations
     __shared__ double s_hyper[6];   // lr_rot, lr_c, beta1, beta2, eps, lr_focal
-    __shared__ double s_loss[STEP_CAMS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = blockIdx.x * STEP_CAMS + warp;
     const int e_begin = k < d.n_cams ? d.cam_off[k] : 0;
@@ -277,14 +276,7 @@ k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gs
             ? camera_update<FOCAL>(d, kc, &s_hi[0][lane], &s_lo[0][lane], STEP_CAMS, s_mv[lane], s_Rc[lane], s_R32[lane], s_hyper,
                             t_step, apply, cam_dst + (size_t)kc * CAMREC)
             : 0.0;
-        s_loss[lane] = bl;
-        __syncwarp(0xffu);
-        if (lane == 0) {
-            double b = 0.0;
-#pragma unroll
-            for (int q = 0; q < STEP_CAMS; ++q) b += s_loss[q];
-            d.cam_loss[blockIdx.x] = b;
-        }
+        if (kc < d.n_cams) d.cam_loss[kc] = bl;
     }
 }
 

@@ -31,7 +31,7 @@ __device__ __forceinline__ void write_camrec(float *rec, const double *R, const 
     for (int q = 0; q < 3; ++q) {
         const float hi = (float)c[q];
         rec[9 + q] = hi;
-        rec[12 + q] = (float)(c[q] - (double)hi);
+        rec[12 + q] = (float)__dsub_rn(c[q], (double)hi);
     }
     rec[15] = (float)s;
 }
@@ -78,8 +78,9 @@ __device__ __forceinline__ void expmap64(const double *phi, double *R) {
 // each step: ~2e-7 -> ~1e-13 -> below FP64 rounding)
 __device__ __forceinline__ double rsqrt64(double x) {
     double y = (double)rsqrtf((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
-    y = y * (1.5 - 0.5 * x * y * y);
+    const double hx = __dmul_rn(-0.5, x);
+    y = __dmul_rn(y, __fma_rn(hx, __dmul_rn(y, y), 1.5));
+    y = __dmul_rn(y, __fma_rn(hx, __dmul_rn(y, y), 1.5));
     return y;
 }
 
@@ -88,38 +89,38 @@ __device__ __forceinline__ double rsqrt64(double x) {
 // that of phi itself, which Adam computes in FP32. For |phi| < 0.1 the Taylor series of a and b
 // through the t^6 terms (truncation below 1e-13); otherwise sin and b = 2 sin^2(t/2) / t^2.
 __device__ __forceinline__ void so3_exp_minus_identity(const float *phi, float *A) {
-    const float th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
+    const float th2 = rdot3(phi[0], phi[0], phi[1], phi[1], phi[2], phi[2]);
     float a, b;
     if (th2 < 0.01f) {
-        a = 1.f - th2 * (1.f / 6.f) * (1.f - th2 * (1.f / 20.f) * (1.f - th2 * (1.f / 42.f)));
-        b = 0.5f * (1.f - th2 * (1.f / 12.f) * (1.f - th2 * (1.f / 30.f) * (1.f - th2 * (1.f / 56.f))));
+        a = rfma(-rmul(th2, 1.f / 6.f), rfma(-rmul(th2, 1.f / 20.f), radd(1.f, -rmul(th2, 1.f / 42.f)), 1.f), 1.f);
+        b = rmul(0.5f, rfma(-rmul(th2, 1.f / 12.f), rfma(-rmul(th2, 1.f / 30.f), radd(1.f, -rmul(th2, 1.f / 56.f)), 1.f), 1.f));
     } else {
-        const float th = sqrtf(th2);
-        const float sh = sinf(0.5f * th);
-        a = sinf(th) / th;
-        b = 2.f * sh * sh / th2;
+        const float th = __fsqrt_rn(th2);
+        const float sh = sinf(rmul(0.5f, th));
+        a = __fdiv_rn(sinf(th), th);
+        b = __fdiv_rn(rmul(rmul(2.f, sh), sh), th2);
     }
     const float K[9] = {0.f, -phi[2], phi[1], phi[2], 0.f, -phi[0], -phi[1], phi[0], 0.f};
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float k2 = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
-            A[3 * r + c] = a * K[3 * r + c] + b * k2;
+            const float k2 = rdot3(K[3 * r], K[c], K[3 * r + 1], K[3 + c], K[3 * r + 2], K[6 + c]);
+            A[3 * r + c] = rfma(b, k2, rmul(a, K[3 * r + c]));
         }
 }
 
 // Gram-Schmidt on the rows: r0 normalised, r1 orthogonalised and normalised, r2 = r0 x r1
 __device__ __forceinline__ void orthonormalize_rows(double *R) {
-    const double n0 = rsqrt64(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
-    for (int q = 0; q < 3; ++q) R[q] *= n0;
-    const double dp = R[0] * R[3] + R[1] * R[4] + R[2] * R[5];
-    for (int q = 0; q < 3; ++q) R[3 + q] -= dp * R[q];
-    const double n1 = rsqrt64(R[3] * R[3] + R[4] * R[4] + R[5] * R[5]);
-    for (int q = 0; q < 3; ++q) R[3 + q] *= n1;
-    R[6] = R[1] * R[5] - R[2] * R[4];
-    R[7] = R[2] * R[3] - R[0] * R[5];
-    R[8] = R[0] * R[4] - R[1] * R[3];
+    const double n0 = rsqrt64(rdot3(R[0], R[0], R[1], R[1], R[2], R[2]));
+    for (int q = 0; q < 3; ++q) R[q] = __dmul_rn(R[q], n0);
+    const double dp = rdot3(R[0], R[3], R[1], R[4], R[2], R[5]);
+    for (int q = 0; q < 3; ++q) R[3 + q] = __fma_rn(-dp, R[q], R[3 + q]);
+    const double n1 = rsqrt64(rdot3(R[3], R[3], R[4], R[4], R[5], R[5]));
+    for (int q = 0; q < 3; ++q) R[3 + q] = __dmul_rn(R[3 + q], n1);
+    R[6] = __fma_rn(R[1], R[5], -__dmul_rn(R[2], R[4]));
+    R[7] = __fma_rn(R[2], R[3], -__dmul_rn(R[0], R[5]));
+    R[8] = __fma_rn(R[0], R[4], -__dmul_rn(R[1], R[3]));
 }
 
 // Chain rule of one image pair (or one range partial of it) to one of its cameras.
@@ -135,26 +136,26 @@ __device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const
                                                 float gscale, float lscale, float *contrib) {
     float Gp[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) Gp[q] = sum[q] * gscale;
+    for (int q = 0; q < 9; ++q) Gp[q] = rmul(sum[q], gscale);
     const float2 cen_i = make_float2(gr[22], gr[23]), cen_j = make_float2(gr[33], gr[34]);
     float M[9], G[9];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        M[3 * a] = Gp[3 * a] + Gp[3 * a + 2] * cen_i.x;
-        M[3 * a + 1] = Gp[3 * a + 1] + Gp[3 * a + 2] * cen_i.y;
+        M[3 * a] = rfma(Gp[3 * a + 2], cen_i.x, Gp[3 * a]);
+        M[3 * a + 1] = rfma(Gp[3 * a + 2], cen_i.y, Gp[3 * a + 1]);
         M[3 * a + 2] = Gp[3 * a + 2];
     }
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        G[b] = M[b] + cen_j.x * M[6 + b];
-        G[3 + b] = M[3 + b] + cen_j.y * M[6 + b];
+        G[b] = rfma(cen_j.x, M[6 + b], M[b]);
+        G[3 + b] = rfma(cen_j.y, M[6 + b], M[3 + b]);
         G[6 + b] = M[6 + b];
     }
     const float *Rn = gr + 9;
     const float tn[3] = {gr[18], gr[19], gr[20]};
     const float inv = gr[21];
     const float *Rj = gr + 24;
-    const float th[3] = {tn[0] * inv, tn[1] * inv, tn[2] * inv};
+    const float th[3] = {rmul(tn[0], inv), rmul(tn[1], inv), rmul(tn[2], inv)};
     // focal: E = [th]_x R_n, the scale gradient from G = dL/dF, then G <- dL/dE
     const float s_i = gr[35], s_j = gr[36];
     {
@@ -164,67 +165,68 @@ __device__ __forceinline__ void pair_chain_rule(const float *gr, int role, const
             float E[9];
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                E[b] = -th[2] * Rn[3 + b] + th[1] * Rn[6 + b];
-                E[3 + b] = th[2] * Rn[b] - th[0] * Rn[6 + b];
-                E[6 + b] = -th[1] * Rn[b] + th[0] * Rn[3 + b];
+                E[b] = rfma(th[1], Rn[6 + b], rmul(-th[2], Rn[3 + b]));
+                E[3 + b] = rfma(-th[0], Rn[6 + b], rmul(th[2], Rn[b]));
+                E[6 + b] = rfma(th[0], Rn[3 + b], rmul(-th[1], Rn[b]));
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    const float ge = G[3 * a + b] * E[3 * a + b];
-                    if (role == 0 ? b < 2 : a < 2) gs = fmaf(ge, role == 0 ? sj[a] : si[b], gs);
+                    const float ge = rmul(G[3 * a + b], E[3 * a + b]);
+                    if (role == 0 ? b < 2 : a < 2) gs = rfma(ge, role == 0 ? sj[a] : si[b], gs);
                 }
         }
         contrib[7] = gs;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) G[3 * a + b] = (G[3 * a + b] * sj[a]) * si[b];
+            for (int b = 0; b < 3; ++b) G[3 * a + b] = rmul(rmul(G[3 * a + b], sj[a]), si[b]);
     }
     float A[9];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        A[b] = -(-th[2] * G[3 + b] + th[1] * G[6 + b]);
-        A[3 + b] = -(th[2] * G[b] - th[0] * G[6 + b]);
-        A[6 + b] = -(-th[1] * G[b] + th[0] * G[3 + b]);
+        A[b] = -rfma(th[1], G[6 + b], rmul(-th[2], G[3 + b]));
+        A[3 + b] = -rfma(-th[0], G[6 + b], rmul(th[2], G[b]));
+        A[6 + b] = -rfma(th[0], G[3 + b], rmul(-th[1], G[b]));
     }
     float GRt[9];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-            GRt[3 * a + b] = G[3 * a] * Rn[3 * b] + G[3 * a + 1] * Rn[3 * b + 1] + G[3 * a + 2] * Rn[3 * b + 2];
+            GRt[3 * a + b] = rdot3(G[3 * a], Rn[3 * b], G[3 * a + 1], Rn[3 * b + 1], G[3 * a + 2], Rn[3 * b + 2]);
     float gth[3], gt[3], gc[3], gp[3];
     vee(GRt, gth);
-    const float dp = th[0] * gth[0] + th[1] * gth[1] + th[2] * gth[2];
+    const float dp = rdot3(th[0], gth[0], th[1], gth[1], th[2], gth[2]);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) gt[q] = (gth[q] - dp * th[q]) * inv;
+    for (int q = 0; q < 3; ++q) gt[q] = rmul(rfma(-dp, th[q], gth[q]), inv);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) gc[q] = Rj[q] * gt[0] + Rj[3 + q] * gt[1] + Rj[6 + q] * gt[2];
+    for (int q = 0; q < 3; ++q) gc[q] = rdot3(Rj[q], gt[0], Rj[3 + q], gt[1], Rj[6 + q], gt[2]);
     if (role == 0) {
         float RtA[9];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) RtA[3 * a + b] = Rn[a] * A[b] + Rn[3 + a] * A[3 + b] + Rn[6 + a] * A[6 + b];
+            for (int b = 0; b < 3; ++b) RtA[3 * a + b] = rdot3(Rn[a], A[b], Rn[3 + a], A[3 + b], Rn[6 + a], A[6 + b]);
         vee(RtA, gp);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             contrib[q] = -gp[q];
             contrib[3 + q] = gc[q];
         }
-        contrib[6] = sum[9] * lscale;
+        contrib[6] = rmul(sum[9], lscale);
     } else {
         float ARt[9];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) ARt[3 * a + b] = A[3 * a] * Rn[3 * b] + A[3 * a + 1] * Rn[3 * b + 1] + A[3 * a + 2] * Rn[3 * b + 2];
+            for (int b = 0; b < 3; ++b)
+                ARt[3 * a + b] = rdot3(A[3 * a], Rn[3 * b], A[3 * a + 1], Rn[3 * b + 1], A[3 * a + 2], Rn[3 * b + 2]);
         vee(ARt, gp);
-        contrib[0] = gp[0] + (tn[1] * gt[2] - tn[2] * gt[1]);
-        contrib[1] = gp[1] + (tn[2] * gt[0] - tn[0] * gt[2]);
-        contrib[2] = gp[2] + (tn[0] * gt[1] - tn[1] * gt[0]);
+        contrib[0] = radd(gp[0], rfma(tn[1], gt[2], rmul(-tn[2], gt[1])));
+        contrib[1] = radd(gp[1], rfma(tn[2], gt[0], rmul(-tn[0], gt[2])));
+        contrib[2] = radd(gp[2], rfma(tn[0], gt[1], rmul(-tn[1], gt[0])));
 #pragma unroll
         for (int q = 0; q < 3; ++q) contrib[3 + q] = -gc[q];
         contrib[6] = 0.f;
@@ -284,21 +286,22 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
     bool ok = isfinite(hi[6 * stride]);
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-        gq[q] = hi[q * stride] + lo[q * stride];
+        gq[q] = radd(hi[q * stride], lo[q * stride]);
         ok = ok && isfinite(gq[q]);
     }
     if (!ok) atomicOr(d.err, ERR_NONFINITE);
     double s_new = s_cur;
     const float b1 = (float)hyper[2], b2 = (float)hyper[3], eps = (float)hyper[4];
     const float lr_r = (float)hyper[0], lr_c = (float)hyper[1];
-    const float bc1 = 1.f - powf(b1, (float)t_step), bc2 = 1.f - powf(b2, (float)t_step);
+    const float bc1 = radd(1.f, -powf(b1, (float)t_step)), bc2 = radd(1.f, -powf(b2, (float)t_step));
     if (FOCAL) {
         const float g1 = (float)g_rho;
-        const float mo = b1 * d.rho_m[kc] + (1.f - b1) * g1;
-        const float vo = b2 * d.rho_v[kc] + (1.f - b2) * g1 * g1;
+        const float mo = rfma(b1, d.rho_m[kc], rmul(radd(1.f, -b1), g1));
+        const float vo = rfma(b2, d.rho_v[kc], rmul(rmul(radd(1.f, -b2), g1), g1));
         d.rho_m[kc] = mo;
         d.rho_v[kc] = vo;
-        const double r = d.rho[kc] - (double)((float)hyper[5] * (mo / bc1) / (sqrtf(vo / bc2) + eps));
+        const double r = d.rho[kc] - (double)__fdiv_rn(rmul((float)hyper[5], __fdiv_rn(mo, bc1)),
+                                                       radd(__fsqrt_rn(__fdiv_rn(vo, bc2)), eps));
         d.rho[kc] = r;
         d.grad_rho[kc] = g_rho;
         s_new = exp(r);
@@ -306,9 +309,10 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
     float dl[6], mo[6], vo[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-        mo[q] = b1 * mv[q] + (1.f - b1) * gq[q];
-        vo[q] = b2 * mv[6 + q] + (1.f - b2) * gq[q] * gq[q];
-        dl[q] = -(q < 3 ? lr_r : lr_c) * (mo[q] / bc1) / (sqrtf(vo[q] / bc2) + eps);
+        mo[q] = rfma(b1, mv[q], rmul(radd(1.f, -b1), gq[q]));
+        vo[q] = rfma(b2, mv[6 + q], rmul(rmul(radd(1.f, -b2), gq[q]), gq[q]));
+        dl[q] = __fdiv_rn(rmul(-(q < 3 ? lr_r : lr_c), __fdiv_rn(mo[q], bc1)),
+                          radd(__fsqrt_rn(__fdiv_rn(vo[q], bc2)), eps));
     }
     float A[9];
     so3_exp_minus_identity(dl, A);
@@ -317,10 +321,11 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            Rn[3 * r + c] = Rc[3 * r + c] + (double)(A[3 * r] * R32[c] + A[3 * r + 1] * R32[3 + c] + A[3 * r + 2] * R32[6 + c]);
+            Rn[3 * r + c] = __dadd_rn(Rc[3 * r + c], (double)rdot3(A[3 * r], R32[c], A[3 * r + 1], R32[3 + c],
+                                                                     A[3 * r + 2], R32[6 + c]));
     orthonormalize_rows(Rn);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) cn[q] = Rc[9 + q] + (double)dl[3 + q];
+    for (int q = 0; q < 3; ++q) cn[q] = __dadd_rn(Rc[9 + q], (double)dl[3 + q]);
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
         const size_t o = (size_t)kc * 6 + q;

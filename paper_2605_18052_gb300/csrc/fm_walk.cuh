@@ -124,6 +124,20 @@ __device__ __forceinline__ void load_E(const float *geo, int n, float *E) {
     E[8] = c;
 }
 
+// Explicitly rounded arithmetic: the compiler never contracts or reassociates these, so a
+// formula written with them gives the same bits in every kernel it is inlined into (the fused
+// optimiser step and the camera-step kernel must agree bit for bit).
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// a0 b0 + a1 b1 + a2 b2 as fma(a2, b2, fma(a1, b1, a0 b0))
+__device__ __forceinline__ float rdot3(float a0, float b0, float a1, float b1, float a2, float b2) {
+    return __fmaf_rn(a2, b2, __fmaf_rn(a1, b1, __fmul_rn(a0, b0)));
+}
+__device__ __forceinline__ double rdot3(double a0, double b0, double a1, double b1, double a2, double b2) {
+    return __fma_rn(a2, b2, __fma_rn(a1, b1, __dmul_rn(a0, b0)));
+}
+
 // epsilon = o2^T E' o1 with o = (x, y, 1)
 __device__ __forceinline__ float epi(const float *E, float x1, float y1, float x2, float y2) {
     const float r0 = fmaf(E[0], x1, fmaf(E[1], y1, E[2]));
@@ -302,10 +316,10 @@ __device__ __forceinline__ bool pair_geometry_regs(const float *cam, const float
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-            Rn[3 * a + b] = Rj[3 * a] * Ri[3 * b] + Rj[3 * a + 1] * Ri[3 * b + 1] + Rj[3 * a + 2] * Ri[3 * b + 2];
-        tn[a] = Rj[3 * a] * dc[0] + Rj[3 * a + 1] * dc[1] + Rj[3 * a + 2] * dc[2];
+            Rn[3 * a + b] = rdot3(Rj[3 * a], Ri[3 * b], Rj[3 * a + 1], Ri[3 * b + 1], Rj[3 * a + 2], Ri[3 * b + 2]);
+        tn[a] = rdot3(Rj[3 * a], dc[0], Rj[3 * a + 1], dc[1], Rj[3 * a + 2], dc[2]);
     }
-    const float nt2 = tn[0] * tn[0] + tn[1] * tn[1] + tn[2] * tn[2];
+    const float nt2 = rdot3(tn[0], tn[0], tn[1], tn[1], tn[2], tn[2]);
     // a baseline below 1e-10 of the centres' magnitude is rounding noise: its direction,
     // and so E_n, is undefined
     float cmax = 1.f;
@@ -313,22 +327,22 @@ __device__ __forceinline__ bool pair_geometry_regs(const float *cam, const float
     for (int q = 0; q < 3; ++q) cmax = fmaxf(cmax, fmaxf(fabsf(hi_i[q]), fabsf(hi_j[q])));
     const float floor2 = 1e-20f * cmax * cmax;
     const bool ok = nt2 > floor2 && isfinite(nt2);
-    const float inv = ok ? 1.0f / sqrtf(nt2) : 0.f;
-    const float th[3] = {tn[0] * inv, tn[1] * inv, tn[2] * inv};
+    const float inv = ok ? __fdiv_rn(1.0f, __fsqrt_rn(nt2)) : 0.f;
+    const float th[3] = {rmul(tn[0], inv), rmul(tn[1], inv), rmul(tn[2], inv)};
     // E = [th]_x R_n, then F = S_j E S_i
     float E[9];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        E[b] = -th[2] * Rn[3 + b] + th[1] * Rn[6 + b];
-        E[3 + b] = th[2] * Rn[b] - th[0] * Rn[6 + b];
-        E[6 + b] = -th[1] * Rn[b] + th[0] * Rn[3 + b];
+        E[b] = rfma(th[1], Rn[6 + b], rmul(-th[2], Rn[3 + b]));
+        E[3 + b] = rfma(-th[0], Rn[6 + b], rmul(th[2], Rn[b]));
+        E[6 + b] = rfma(th[0], Rn[3 + b], rmul(-th[1], Rn[b]));
     }
     {
         const float si[3] = {s_i, s_i, 1.f}, sj[3] = {s_j, s_j, 1.f};
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) E[3 * a + b] = (E[3 * a + b] * sj[a]) * si[b];
+            for (int b = 0; b < 3; ++b) E[3 * a + b] = rmul(rmul(E[3 * a + b], sj[a]), si[b]);
     }
     // E' = T_j^T E T_i with T = [[1,0,cx],[0,1,cy],[0,0,1]] (keypoints stored as offsets o = x - c)
     const float2 cen_i = cen[i], cen_j = cen[j];
@@ -336,12 +350,12 @@ __device__ __forceinline__ bool pair_geometry_regs(const float *cam, const float
     for (int a = 0; a < 2; ++a) {
         g[3 * a] = E[3 * a];
         g[3 * a + 1] = E[3 * a + 1];
-        g[3 * a + 2] = E[3 * a] * cen_i.x + E[3 * a + 1] * cen_i.y + E[3 * a + 2];
+        g[3 * a + 2] = rfma(E[3 * a + 1], cen_i.y, rfma(E[3 * a], cen_i.x, E[3 * a + 2]));
     }
-    const float m20 = E[6], m21 = E[7], m22 = E[6] * cen_i.x + E[7] * cen_i.y + E[8];
-    g[6] = cen_j.x * g[0] + cen_j.y * g[3] + m20;
-    g[7] = cen_j.x * g[1] + cen_j.y * g[4] + m21;
-    g[8] = cen_j.x * g[2] + cen_j.y * g[5] + m22;
+    const float m20 = E[6], m21 = E[7], m22 = rfma(E[7], cen_i.y, rfma(E[6], cen_i.x, E[8]));
+    g[6] = rfma(cen_j.y, g[3], rfma(cen_j.x, g[0], m20));
+    g[7] = rfma(cen_j.y, g[4], rfma(cen_j.x, g[1], m21));
+    g[8] = rfma(cen_j.y, g[5], rfma(cen_j.x, g[2], m22));
 #pragma unroll
     for (int k = 0; k < 9; ++k) g[9 + k] = Rn[k];
     g[18] = tn[0];
@@ -374,20 +388,20 @@ __device__ __forceinline__ void pair_geometry(const DevProblem &d, int n, int i,
     for (int k = 0; k < GEO / 4; ++k) out[k] = make_float4(g[4 * k], g[4 * k + 1], g[4 * k + 2], g[4 * k + 3]);
 }
 
-// Loss total of a camera-step launch (FP64, fixed order over its blocks) and `count` steps
-// added to the step count. One block of NT threads (NT divides FIN_THREADS); the
-// summation order is that of FIN_THREADS threads whatever NT is, so every launch that
-// finishes a step produces the same bits.
+// Loss total of an optimiser step (FP64, fixed order over the n_loss per-camera shares in
+// cam_loss) and `count` steps added to the step count. One block of NT threads (NT divides
+// FIN_THREADS); the summation order is that of FIN_THREADS threads whatever NT is, so every
+// launch that finishes a step produces the same bits.
 constexpr int FIN_THREADS = 256;
 
 template <int NT = FIN_THREADS>
-__device__ __forceinline__ void finish_step(const DevProblem &d, int n_blocks, int count) {
+__device__ __forceinline__ void finish_step(const DevProblem &d, int n_loss, int count) {
     static_assert(FIN_THREADS % NT == 0, "block must divide FIN_THREADS");
     __shared__ double red[FIN_THREADS];
 #pragma unroll
     for (int v = threadIdx.x; v < FIN_THREADS; v += NT) {
         double s = 0.0;
-        for (int q = v; q < n_blocks; q += FIN_THREADS) s += d.cam_loss[q];
+        for (int q = v; q < n_loss; q += FIN_THREADS) s += d.cam_loss[q];
         red[v] = s;
     }
     __syncthreads();
