@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(CTA_WARPS * 32) k_residuals(DevProblem d, floa
 __global__ void k_cam_prep(DevProblem d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n_cams) return;
-    write_camrec(d.cam + (size_t)k * CAMREC, d.R + 9 * (size_t)k, d.c + 3 * (size_t)k, camera_scale(d, k));
+    write_camrec(d.cam + (size_t)k * CAMREC, d.R + 9 * (size_t)k, d.c + 3 * (size_t)k, (float)camera_scale(d, k));
 }
 
 // prev_loss > 0: this pass follows an optimiser step with that many per-camera loss shares;
@@ -351,7 +351,7 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply, int next_geo)
     __shared__ __align__(16) float s_geo[STEP_CAMS][32][GEO];
     __shared__ float s_mv[STEP_CAMS][12];     // Adam m (6) and v (6) of the block's cameras
     __shared__ double s_Rc[STEP_CAMS][12];    // R (9) and c (3) of the block's cameras
-    __shared__ float s_R32[STEP_CAMS][9];     // their FP32 record rotations
+    __shared__ float s_R32[STEP_CAMS][10];    // their records' rotations (9) and keypoint scale
     __shared__ double s_hyper[6];   // lr_rot, lr_c, beta1, beta2, eps, lr_focal
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = blockIdx.x * STEP_CAMS + warp;
@@ -362,7 +362,7 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply, int next_geo)
             if (cam0 + cc < d.n_cams) {
                 s_mv[cc][q] = q < 6 ? d.m[(size_t)(cam0 + cc) * 6 + q] : d.v[(size_t)(cam0 + cc) * 6 + q - 6];
                 s_Rc[cc][q] = q < 9 ? d.R[(size_t)(cam0 + cc) * 9 + q] : d.c[(size_t)(cam0 + cc) * 3 + q - 9];
-                if (q < 9) s_R32[cc][q] = d.cam[(size_t)(cam0 + cc) * CAMREC + q];
+                if (q < 10) s_R32[cc][q] = d.cam[(size_t)(cam0 + cc) * CAMREC + (q < 9 ? q : 15)];
             }
         }
         if (threadIdx.x < 6) s_hyper[threadIdx.x] = d.hyper[threadIdx.x];
@@ -454,52 +454,36 @@ k_camera_step(DevProblem d, float gscale, float lscale, int apply, int next_geo)
     }
 }
 
-// Adam step with a given gradient (d.grad), one camera per thread: FP32 moments, FP64
-// exponential map, re-orthonormalisation and centre update; thread 0 advances the step.
+// Adam step with a given gradient (d.grad, FP64), one camera per thread: the same update as the
+// camera-step kernel (camera_update with the gradient split into FP32 hi + lo parts, whose FP32
+// sum is the gradient rounded to FP32, as there); the step count is advanced by k_bump_step.
 __global__ void k_apply_gradient(DevProblem d) {
     const int kc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kc >= d.n_cams) return;
     const long long t_step = *d.step + 1;
-    if (kc < d.n_cams) {
-        const float b1 = (float)d.hyper[2], b2 = (float)d.hyper[3], eps = (float)d.hyper[4];
-        const float lr_r = (float)d.hyper[0], lr_c = (float)d.hyper[1];
-        const float bc1 = 1.f - powf(b1, (float)t_step), bc2 = 1.f - powf(b2, (float)t_step);
-        double dl[6], Rk[9], ck[3];
-        float mo[6], vo[6];
+    float hi[STEP_VALS], lo[STEP_VALS], mv[12], rec[10];
+    double Rc[12], hyper[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const size_t o = (size_t)kc * 6 + q;
-            const double g64 = d.grad[o];
-            if (!isfinite(g64)) atomicOr(d.err, ERR_NONFINITE);
-            const float gq = (float)g64;
-            mo[q] = b1 * d.m[o] + (1.f - b1) * gq;
-            vo[q] = b2 * d.v[o] + (1.f - b2) * gq * gq;
-            dl[q] = (double)(-(q < 3 ? lr_r : lr_c) * (mo[q] / bc1) / (sqrtf(vo[q] / bc2) + eps));
-        }
-#pragma unroll
-        for (int q = 0; q < 9; ++q) Rk[q] = d.R[(size_t)kc * 9 + q];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) ck[q] = d.c[(size_t)kc * 3 + q];
-        double Ex[9], Rn[9], cn[3];
-        expmap64(dl, Ex);
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                Rn[3 * r + c] = Ex[3 * r] * Rk[c] + Ex[3 * r + 1] * Rk[3 + c] + Ex[3 * r + 2] * Rk[6 + c];
-        orthonormalize_rows(Rn);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) cn[q] = ck[q] + dl[3 + q];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            d.m[(size_t)kc * 6 + q] = mo[q];
-            d.v[(size_t)kc * 6 + q] = vo[q];
-        }
-#pragma unroll
-        for (int q = 0; q < 9; ++q) d.R[(size_t)kc * 9 + q] = Rn[q];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) d.c[(size_t)kc * 3 + q] = cn[q];
-        write_camrec(d.cam + (size_t)kc * CAMREC, Rn, cn, camera_scale(d, kc));
+    for (int q = 0; q < STEP_VALS; ++q) {
+        const double g = q < 6 ? d.grad[(size_t)kc * 6 + q] : 0.0;
+        hi[q] = (float)g;
+        lo[q] = (float)__dsub_rn(g, (double)hi[q]);
     }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        mv[q] = d.m[(size_t)kc * 6 + q];
+        mv[6 + q] = d.v[(size_t)kc * 6 + q];
+        hyper[q] = d.hyper[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        Rc[q] = d.R[(size_t)kc * 9 + q];
+        rec[q] = d.cam[(size_t)kc * CAMREC + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) Rc[9 + q] = d.c[(size_t)kc * 3 + q];
+    rec[9] = d.cam[(size_t)kc * CAMREC + 15];
+    camera_update<false>(d, kc, hi, lo, 1, mv, Rc, rec, hyper, t_step, 1, d.cam + (size_t)kc * CAMREC);
 }
 
 __global__ void k_bump_step(DevProblem d) { *d.step += 1; }

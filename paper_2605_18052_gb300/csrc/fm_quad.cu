@@ -169,7 +169,7 @@ k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gs
     __shared__ float s_hi[STEP_VALS][STEP_CAMS], s_lo[STEP_VALS][STEP_CAMS];
     __shared__ float s_mv[STEP_CAMS][12];
     __shared__ double s_Rc[STEP_CAMS][12];
-    __shared__ float s_R32[STEP_CAMS][9];     // the cameras' FP32 record rotations
+    __shared__ float s_R32[STEP_CAMS][10];    // the cameras' records' rotations (9) and keypoint scale
     __shared__ double s_hyper[6];   // lr_rot, lr_c, beta1, beta2, eps, lr_focal
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = blockIdx.x * STEP_CAMS + warp;
@@ -196,7 +196,7 @@ k_quad_step(DevProblem d, int it, const float *cam_src, float *cam_dst, float gs
             if (cam0 + cc < d.n_cams) {
                 s_mv[cc][q] = q < 6 ? d.m[(size_t)(cam0 + cc) * 6 + q] : d.v[(size_t)(cam0 + cc) * 6 + q - 6];
                 s_Rc[cc][q] = q < 9 ? d.R[(size_t)(cam0 + cc) * 9 + q] : d.c[(size_t)(cam0 + cc) * 3 + q - 9];
-                if (q < 9) s_R32[cc][q] = cam_src[(size_t)(cam0 + cc) * CAMREC + q];
+                if (q < 10) s_R32[cc][q] = cam_src[(size_t)(cam0 + cc) * CAMREC + (q < 9 ? q : 15)];
             }
         }
         if (threadIdx.x < 6) s_hyper[threadIdx.x] = d.hyper[threadIdx.x];

@@ -24,7 +24,7 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float bhi, flo
 
 // ---- per camera: pose record --------------------------------------------------------------------
 // R (9 floats), centre as hi + lo floats (3 + 3), keypoint scale s (focal refinement)
-__device__ __forceinline__ void write_camrec(float *rec, const double *R, const double *c, double s) {
+__device__ __forceinline__ void write_camrec(float *rec, const double *R, const double *c, float s) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) rec[i] = (float)R[i];
 #pragma unroll
@@ -33,7 +33,7 @@ __device__ __forceinline__ void write_camrec(float *rec, const double *R, const 
         rec[9 + q] = hi;
         rec[12 + q] = (float)__dsub_rn(c[q], (double)hi);
     }
-    rec[15] = (float)s;
+    rec[15] = s;
 }
 
 // keypoint scale of camera k: exp(rho_k), 1 without focal state
@@ -45,33 +45,6 @@ __device__ __forceinline__ void vee(const float *M, float *v) {
     v[0] = M[7] - M[5];
     v[1] = M[2] - M[6];
     v[2] = M[3] - M[1];
-}
-
-// Exp(phi) by Rodrigues' formula, R = I + a K + b K^2 with K = [phi]_x. For |phi| < 0.1
-// (every Adam step: |phi| <= lr) a = sin(t)/t and b = (1 - cos(t))/t^2 come from their Taylor
-// series in t^2 through the t^8 terms (truncation < 3e-18, below half an FP64 ulp of 1),
-// which avoids FP64 sin/cos/sqrt/division on GB300's narrow FP64 pipe.
-__device__ __forceinline__ void expmap64(const double *phi, double *R) {
-    const double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
-    double a, b;
-    if (th2 < 0.01) {
-        a = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0))));
-        b = 0.5 * (1.0 - th2 * (1.0 / 12.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0) * (1.0 - th2 * (1.0 / 90.0)))));
-    } else {
-        const double th = sqrt(th2);
-        double sn, cs;
-        sincos(th, &sn, &cs);
-        a = sn / th;
-        b = (1.0 - cs) / th2;
-    }
-    const double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double k2 = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
-            R[3 * r + c] = (r == c ? 1.0 : 0.0) + a * K[3 * r + c] + b * k2;
-        }
 }
 
 // 1/sqrt(x) in FP64: an FP32 seed refined by two Newton steps (the relative error squares
@@ -252,21 +225,26 @@ __device__ __forceinline__ void warp_two_sum_reduce(float *hi, float *lo) {
 // moments) and the new pose: R <- R + (Exp(phi) - I) R and c <- c + delta_c in FP64, where the
 // small increment (Exp(phi) - I) R is formed in FP32 from the camera's FP32 record rotation R32
 // (its error, a few 1e-7 |phi|, is of the order of phi's own FP32 error), then Gram-Schmidt on
-// the rows in FP64 and the new camera record at rec_out. hi/lo hold STEP_VALS values (6 pose
-// gradient components, the loss, the keypoint-scale gradient) `stride` apart; mv = the
-// camera's Adam m (6) and v (6); Rc = its R (9) and c (3) in FP64; hyper = lr_rot, lr_c,
-// beta1, beta2, eps, lr_focal. With focal refinement rho = log s takes its own Adam step
-// (gradient s dL/ds). Returns the camera's loss share.
+// the rows in FP64 on every eighth step (steps 1, 9, 17, ...) and the new camera record at
+// rec_out. hi/lo hold STEP_VALS values (6 pose gradient components, the loss, the
+// keypoint-scale gradient) `stride` apart; mv = the camera's Adam m (6) and v (6); Rc = its R
+// (9) and c (3) in FP64; rec = its current record's rotation (9 floats) and keypoint scale
+// (rec[9]); hyper = lr_rot, lr_c, beta1, beta2, eps, lr_focal. With focal refinement
+// rho = log s takes its own Adam step (gradient s dL/ds); without, the record keeps its scale.
+// Returns the camera's loss share.
 // GB300 executes FP64 on a narrow pipe at whole-warp cost per instruction, and every block of a
 // step reaches this phase at the same moment, so the update keeps its FP64 work to the state
-// itself (about 90 operations: the two sums, the re-orthonormalisation and the record).
+// itself: the two sums and the record (about 45 operations), and the re-orthonormalisation
+// (about 40) only every eighth step. Between two of them R leaves SO(3) by the FP32 rounding of
+// the increments, a few 1e-7 |phi| per step, far below the FP32 camera record's resolution.
 template <bool FOCAL>
 __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, const float *hi, const float *lo,
-                                                int stride, const float *mv, const double *Rc, const float *R32,
+                                                int stride, const float *mv, const double *Rc, const float *rec,
                                                 const double *hyper, long long t_step, int apply,
                                                 float *rec_out) {
+    const float *R32 = rec;
     const double bl = (double)hi[6 * stride] + (double)lo[6 * stride];
-    const double s_cur = camera_scale(d, kc);
+    const double s_cur = FOCAL ? camera_scale(d, kc) : 1.0;
     const double g_rho = FOCAL ? s_cur * ((double)hi[7 * stride] + (double)lo[7 * stride]) : 0.0;
     if (!apply) {
         bool ok = isfinite(hi[6 * stride]);
@@ -290,7 +268,7 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
         ok = ok && isfinite(gq[q]);
     }
     if (!ok) atomicOr(d.err, ERR_NONFINITE);
-    double s_new = s_cur;
+    float s_new = rec[9];
     const float b1 = (float)hyper[2], b2 = (float)hyper[3], eps = (float)hyper[4];
     const float lr_r = (float)hyper[0], lr_c = (float)hyper[1];
     const float bc1 = radd(1.f, -powf(b1, (float)t_step)), bc2 = radd(1.f, -powf(b2, (float)t_step));
@@ -304,7 +282,7 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
                                                        radd(__fsqrt_rn(__fdiv_rn(vo, bc2)), eps));
         d.rho[kc] = r;
         d.grad_rho[kc] = g_rho;
-        s_new = exp(r);
+        s_new = (float)exp(r);
     }
     float dl[6], mo[6], vo[6];
 #pragma unroll
@@ -323,7 +301,7 @@ __device__ __forceinline__ double camera_update(const DevProblem &d, int kc, con
         for (int c = 0; c < 3; ++c)
             Rn[3 * r + c] = __dadd_rn(Rc[3 * r + c], (double)rdot3(A[3 * r], R32[c], A[3 * r + 1], R32[3 + c],
                                                                      A[3 * r + 2], R32[6 + c]));
-    orthonormalize_rows(Rn);
+    if ((t_step & 7) == 1) orthonormalize_rows(Rn);
 #pragma unroll
     for (int q = 0; q < 3; ++q) cn[q] = __dadd_rn(Rc[9 + q], (double)dl[3 + q]);
 #pragma unroll

@@ -360,10 +360,34 @@ def test_two_shards_on_one_gpu_sum_to_the_whole_problem():
         R0s, t0s = shards[0].get_poses()
         R1s, _ = shards[1].get_poses()
     np.testing.assert_array_equal(R0s, R1s)
+    # the summed gradient differs from the whole problem's in its last bits, and Adam's
+    # normalisation turns a last-bit difference of a near-zero component into a visible step
+    # difference; as for the oracle comparison, the paths agree to a small fraction of one step
+    # (lr_rot = 1e-2 rad by default)
     ang = np.degrees(np.arccos(np.clip((np.einsum("nab,nab->n", Rw, R0s) - 1) / 2, -1, 1)))
-    assert ang.max() < 1e-3
+    assert ang.max() < 0.02 * np.degrees(1e-2)
     for s in shards:
         s.close()
+
+
+def test_apply_gradient_is_the_optimiser_step():
+    # fm_apply_gradient with the problem's own gradient takes the same step as fm_step, bit for
+    # bit: the FP64 gradient rounds to the FP32 value the camera step uses (hi of its
+    # compensated hi + lo sum), and both run the same update
+    sc = _scene("sphere128", seed=10)
+    R0, t0 = sc.R_init.numpy(), sc.t_init.numpy()
+    with _gpu_problem(sc, R0, t0) as a, _gpu_problem(sc, R0, t0) as b:
+        a.irls_weights(0.05)
+        b.irls_weights(0.05)
+        for _ in range(10):
+            a.apply_gradient(a.loss_grad()[1])
+            b.step(1)
+        Ra, ta = a.get_poses()
+        Rb, tb = b.get_poses()
+        assert a.get_state()[2] == b.get_state()[2] == 10
+        np.testing.assert_array_equal(Ra, Rb)
+        np.testing.assert_array_equal(ta, tb)
+        assert a.loss_grad()[0] == b.loss_grad()[0]
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
