@@ -74,7 +74,9 @@ def peaks():
 # combined hash matches the one recorded with it
 KERNEL_SOURCES = {
     "stream_loss": ("fm_kernels.cu", "fm_walk.cuh", "fm_internal.cuh"),
+    "stream_reweight": ("fm_kernels.cu", "fm_walk.cuh", "fm_internal.cuh"),
     "quad_accumulate": ("fm_quad.cu", "fm_walk.cuh", "fm_internal.cuh"),
+    "learned_loss": ("fm_mlp.cu", "fm_tcgen05.cuh", "fm_walk.cuh", "fm_internal.cuh"),
 }
 
 
@@ -408,13 +410,15 @@ QUAD_FMA_OPS = 66
 FP32_LANES = 152 * 128
 
 
-def pass_entry(name, storage, n_pp, ms, launches, peak, sm_mhz):
+def pass_entry(name, storage, config, n_pp, ms, launches, peak, sm_mhz):
     if not launches:
         return {"unavailable": "no timed launches"}
     us = ms / launches * 1e3
     gbs = n_pp * PASS_BYTES[name][storage] / (us * 1e-6) / 1e9
     e = {"us_per_launch": us, "launches": launches, "bytes_per_point_pair": PASS_BYTES[name][storage],
          "achieved_gbs": gbs, "hbm_frac": gbs / peak, "g_point_pairs_per_s": n_pp / (us * 1e-6) / 1e9}
+    if name in KERNEL_SOURCES:   # DRAM bytes per launch from the committed ncu summary, if current
+        e["traffic"] = profiled_traffic(f"{name}_{storage}_{config}")
     if name == "quad_accumulate":
         t = n_pp * QUAD_FMA_OPS / (us * 1e-6) / 1e12
         pk = FP32_LANES * (sm_mhz or 2070.0) * 1e6 / 1e12
@@ -428,7 +432,8 @@ def passes_section(args, gp, sc, sch, n_pp, peak, sm_mhz, reweight_timed):
     roofline (and the FP32 pipe for the form pass)."""
     import numpy as np
     from paper_2605_18052_gb300 import Mlp, binding
-    out = {"stream_reweight": pass_entry("stream_reweight", args.storage, n_pp, *reweight_timed, peak, sm_mhz)}
+    out = {"stream_reweight": pass_entry("stream_reweight", args.storage, args.config, n_pp, *reweight_timed, peak,
+                                         sm_mhz)}
     gp.enable_kernel_timing(True)
     for k in range(args.steps // 4 + 3):
         gp.irls_preaggregate(sch.tau(k % sch.rounds))
@@ -436,7 +441,7 @@ def passes_section(args, gp, sc, sch, n_pp, peak, sm_mhz, reweight_timed):
     gp.pass_time(binding.PASS_QUAD_ACCUMULATE)      # drop the warm-up launches
     for k in range(args.steps // 4):
         gp.irls_preaggregate(sch.tau(k % sch.rounds))
-    out["quad_accumulate"] = pass_entry("quad_accumulate", args.storage, n_pp,
+    out["quad_accumulate"] = pass_entry("quad_accumulate", args.storage, args.config, n_pp,
                                         *gp.pass_time(binding.PASS_QUAD_ACCUMULATE), peak, sm_mhz)
     path = os.path.join(ROOT, "paper_2605_18052_gb300", "data", "mlp_inlier.npy")
     if os.path.exists(path):
@@ -450,9 +455,9 @@ def passes_section(args, gp, sc, sch, n_pp, peak, sm_mhz, reweight_timed):
         gp.pass_time(binding.PASS_PAIR_STATS)
         for r in range(3, 3 + args.steps // 4):
             gp.step_learned(net, sch.tau(r), sch.tau(r), r, 1)
-        out["learned_loss"] = pass_entry("learned_loss", args.storage, n_pp,
+        out["learned_loss"] = pass_entry("learned_loss", args.storage, args.config, n_pp,
                                          *gp.pass_time(binding.PASS_LEARNED_LOSS), peak, sm_mhz)
-        out["pair_stats"] = pass_entry("pair_stats", args.storage, n_pp,
+        out["pair_stats"] = pass_entry("pair_stats", args.storage, args.config, n_pp,
                                        *gp.pass_time(binding.PASS_PAIR_STATS), peak, sm_mhz)
         net.close()
     gp.enable_kernel_timing(False)
