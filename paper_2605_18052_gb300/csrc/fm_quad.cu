@@ -14,10 +14,25 @@
 // 6 x 6 = 36 distinct values M[u][v] = sum w m2_u m1_v over the monomials
 //   m2 = (x2^2, x2 y2, x2, y2^2, y2, 1),  m1 = (x1^2, x1 y1, x1, y1^2, y1, 1),
 // with W[3p+q][3r+s] = M[sym(p,r)][sym(q,s)], sym the index of the unordered pair in
-// (00, 01, 02, 11, 12, 22). Per point pair that is 36 multiply-adds instead of 45.
+// (00, 01, 02, 11, 12, 22). Per point pair that is 36 multiply-adds instead of 45, issued as 18
+// packed pairs.
 #include "fm_step.cuh"
 
 namespace fm {
+
+// d0 = fma(a0, b0, d0) and d1 = fma(a1, b1, d1) as one packed FP32 instruction (fma.rn.f32x2):
+// each lane rounds once, exactly as fmaf, so the sums keep their bits, and the pass issues one
+// instruction where it issued two (it is bound by instruction issue, not by the FP32 pipe)
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%0, %1};\n\t"
+        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rc;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
 
 // REWEIGHT: the IRLS weights are computed from the residual at the same poses (and written,
 // quantised as the storage keeps them) before they enter the sums
@@ -53,14 +68,14 @@ struct QuadBody {
         for (int p = 0; p < 3; ++p)
 #pragma unroll
             for (int q = 0; q < 3; ++q) acc[1 + 3 * p + q] = fmaf(t2[p], o1[q], acc[1 + 3 * p + q]);
-        // M[u][v] += (w m2_u) m1_v
+        // M[u][v] += (w m2_u) m1_v, two neighbouring entries of a row per packed instruction
         const float wx2 = w * x2, wy2 = w * y2;
         const float u[6] = {wx2 * x2, wx2 * y2, wx2, wy2 * y2, wy2, w};
         const float v[6] = {x1 * x1, x1 * y1, x1, y1 * y1, y1, 1.f};
 #pragma unroll
         for (int a = 0; a < 6; ++a)
 #pragma unroll
-            for (int b = 0; b < 6; ++b) acc[10 + 6 * a + b] = fmaf(u[a], v[b], acc[10 + 6 * a + b]);
+            for (int b = 0; b < 6; b += 2) fma2(acc[10 + 6 * a + b], acc[10 + 6 * a + b + 1], u[a], u[a], v[b], v[b + 1]);
     }
     __device__ __forceinline__ void segment_end(int seg, int r, int lane, bool) {
 #pragma unroll
