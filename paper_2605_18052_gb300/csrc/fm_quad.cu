@@ -20,20 +20,6 @@
 
 namespace fm {
 
-// d0 = fma(a0, b0, d0) and d1 = fma(a1, b1, d1) as one packed FP32 instruction (fma.rn.f32x2):
-// each lane rounds once, exactly as fmaf, so the sums keep their bits, and the pass issues one
-// instruction where it issued two (it is bound by instruction issue, not by the FP32 pipe)
-__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
-    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
-        "mov.b64 ra, {%2, %3};\n\t"
-        "mov.b64 rb, {%4, %5};\n\t"
-        "mov.b64 rc, {%0, %1};\n\t"
-        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
-        "mov.b64 {%0, %1}, rc;\n\t}"
-        : "+f"(d0), "+f"(d1)
-        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
-}
-
 // REWEIGHT: the IRLS weights are computed from the residual at the same poses (and written,
 // quantised as the storage keeps them) before they enter the sums
 template <int STORE, bool REWEIGHT>
@@ -68,7 +54,8 @@ struct QuadBody {
         for (int p = 0; p < 3; ++p)
 #pragma unroll
             for (int q = 0; q < 3; ++q) acc[1 + 3 * p + q] = fmaf(t2[p], o1[q], acc[1 + 3 * p + q]);
-        // M[u][v] += (w m2_u) m1_v, two neighbouring entries of a row per packed instruction
+        // M[u][v] += (w m2_u) m1_v, two neighbouring entries of a row per packed instruction (the
+        // pass is bound by instruction issue, not by the FP32 pipe)
         const float wx2 = w * x2, wy2 = w * y2;
         const float u[6] = {wx2 * x2, wx2 * y2, wx2, wy2 * y2, wy2, w};
         const float v[6] = {x1 * x1, x1 * y1, x1, y1 * y1, y1, 1.f};

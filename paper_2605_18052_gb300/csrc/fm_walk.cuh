@@ -225,6 +225,40 @@ __device__ __forceinline__ void walk_range(const DevProblem &d, int r, int lane,
     body.segment_end(seg, r, lane, true);
 }
 
+// ---- packed FP32 pairs -----------------------------------------------------------------------------
+// Two lanes of FP32 arithmetic in one instruction (fma/mul/add.rn.f32x2): each lane rounds once,
+// exactly as the scalar operation, so results keep their bits while the streaming passes, which
+// are close to bound by instruction issue, issue one instruction where they issued two.
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%0, %1};\n\t"
+        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rc;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void mul2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rc, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rc;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+// d0 += b0, d1 += b1
+__device__ __forceinline__ void add2(float &d0, float &d1, float b0, float b1) {
+    asm("{\n\t.reg .b64 rb, rc;\n\t"
+        "mov.b64 rb, {%2, %3};\n\t"
+        "mov.b64 rc, {%0, %1};\n\t"
+        "add.rn.f32x2 rc, rc, rb;\n\t"
+        "mov.b64 {%0, %1}, rc;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(b0), "f"(b1));
+}
+
 // ---- loss + adjoint -----------------------------------------------------------------------------
 // acc[0..8] = sum s * o2 o1^T (row-major), acc[9] = sum of loss terms, with s = w*eps (IRLS,
 // the factor 2/Z is applied later) or sign(eps) (L1). Each finished (image pair, warp range)
@@ -248,15 +282,12 @@ struct LossBody {
             s = e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f);
             acc[9] += fabsf(e);
         }
-        const float a = s * x2, b = s * y2;
-        acc[0] = fmaf(a, x1, acc[0]);
-        acc[1] = fmaf(a, y1, acc[1]);
-        acc[2] += a;
-        acc[3] = fmaf(b, x1, acc[3]);
-        acc[4] = fmaf(b, y1, acc[4]);
-        acc[5] += b;
-        acc[6] = fmaf(s, x1, acc[6]);
-        acc[7] = fmaf(s, y1, acc[7]);
+        float a, b;   // s x2, s y2
+        mul2(a, b, s, s, x2, y2);
+        fma2(acc[0], acc[1], a, a, x1, y1);
+        add2(acc[2], acc[5], a, b);
+        fma2(acc[3], acc[4], b, b, x1, y1);
+        fma2(acc[6], acc[7], s, s, x1, y1);
         acc[8] += s;
     }
     __device__ __forceinline__ void segment_begin(int) {}
